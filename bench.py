@@ -1,0 +1,348 @@
+"""Benchmark: time-to-solution of s generalized eigenpairs (A X = B X Lambda)
+through the KE route on one GB300, plus roofline and CPU-oracle baseline.
+
+Workload (default): n = 16384, s = 100 smallest, float64, synthetic pencil
+A = U^T Q diag(lambda) Q^T U, B = G G^T / n + I, lambda ~ U(0, 1000) (the
+stand-in for the paper's n ~ 10^4 molecular-dynamics / DFT pencils).
+
+One step = one full gsyeig_solve (potrf, sygst, Lanczos with restarts, Ritz
+vectors, back-transform) on inputs already resident in HBM; A and B are
+restored from pristine device copies between steps, outside the timed
+interval.  Inputs (2 x 2.1 GB) are far larger than the 129 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs independent replicas, one problem per GPU, no
+collective on the data path; the reported time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution for s gen. eigenpairs @rel. residual ≤1e-10"
+HBM_GBS = 6797.9
+BF16_TFLOPS = 1906.4
+FP64_OVER_BF16_NOMINAL = 1.25 / 2250.0  # GB300 nominal dense FP64 / bf16
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(value: float, ws: int, device=None) -> float:
+    """Max of a float over ranks (identity when ws == 1)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    it was taken on the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, e["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if h != e.get("source_sha256_16"):
+        return None
+    return e
+
+
+def cpu_oracle_sample(n_full: int, s_full: int, n_sample: int):
+    """Time the oracle on the leading n_sample x n_sample sub-pencil and
+    scale by (n_full / n_sample)^3 (every stage of the oracle is O(n^3))."""
+    import inputs
+    import oracle
+
+    s = max(1, round(s_full * n_sample / n_full))
+    A, B, _ = (t.numpy() for t in inputs.make_pencil(n_sample, seed=0))
+    t0 = time.perf_counter()
+    oracle.gsyeig(A, B, s, vectors="invit")
+    dt = time.perf_counter() - t0
+    scale = (n_full / n_sample) ** 3
+    return {"value": dt * scale, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"oracle on the leading {n_sample}x{n_sample} sub-pencil (s={s}), {dt:.2f} s measured, "
+                      f"scaled by (n/{n_sample})^3 = {scale:.0f}"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    n_sample = args.cpu_sample_n
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args.n, args.s, n_sample)
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(args.n, args.s, n_sample))
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "n": args.n, "s": args.s, "which": "smallest"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "bench.py needs a CUDA GPU"}), flush=True)
+        return 2
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist(ws, "nccl")
+    import inputs
+    from paper_1111_6374_gb300 import Solver, kernel_launches
+
+    n, s = args.n, args.s
+    A0, B0, lam = inputs.make_pencil(n, seed=args.seed + rank, device=dev)
+    A = torch.empty_like(A0)
+    B = torch.empty_like(B0)
+    solver = Solver(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def restore():
+        A.copy_(A0)
+        B.copy_(B0)
+
+    for _ in range(args.warmup):
+        restore()
+        w, X, info = solver.solve(A, B, s, overwrite=True)
+    torch.cuda.synchronize()
+    solver.set_options(profile=1)
+    times, infos = [], []
+    l_before = kernel_launches()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            restore()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            w, X, info = solver.solve(A, B, s, overwrite=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = (kernel_launches() - l_before) // max(1, args.steps)
+    solver.set_options(profile=0)
+    ms = statistics.mean(times)
+    ms_all = max_over_ranks(ms, ws, dev)
+
+    # accuracy of the last timed solve against the constructed spectrum and (A, B)
+    rel = float(((w - lam[:s]).abs() / lam[:s].abs()).max())
+    R = A0 @ X - (B0 @ X) * w
+    nA = _power(A0)
+    nB = _power(B0)
+    eta = float((R.norm(dim=0) / ((nA + w.abs() * nB) * X.norm(dim=0))).max())
+    orth = float((X.T @ (B0 @ X) - torch.eye(s, device=dev, dtype=X.dtype)).abs().max())
+
+    # end to end: host buffers through the same C-ABI call, copies inside the timed interval
+    Ah = A0.cpu().pin_memory()
+    Bh = B0.cpu().pin_memory()
+    solver.solve(Ah, Bh, s)  # warm the staging buffers
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, args.e2e_steps))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        wh, Xh, _ = solver.solve(Ah, Bh, s)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = statistics.mean(e2e_times)
+    e2e = max_over_ranks(e2e, ws, dev)
+
+    if rank != 0:
+        return 0
+    peaks, src = load_peaks()
+    fp64_peak = peaks.get("bf16_tflops", BF16_TFLOPS) * FP64_OVER_BF16_NOMINAL
+    g_ms = sum(i["gemm_ms"] for i in infos)
+    g_fl = sum(i["gemm_flops"] for i in infos)
+    g_n = sum(i["gemm_launches"] for i in infos)
+    s_ms = sum(i["symv_ms"] for i in infos)
+    s_fl = sum(i["symv_flops"] for i in infos)
+    s_by = sum(i["symv_bytes"] for i in infos)
+    s_n = sum(i["symv_launches"] for i in infos)
+    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+    tr = kernel_traffic("k_dgemm")
+    roof = {"kernel": "k_dgemm (FP64 GEMM engine of gs1/gs2/bt1)", "bound": "alu", "achieved": achieved,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+            "peak_source": f"{src} bf16 {peaks.get('bf16_tflops', BF16_TFLOPS)} TF/s x nominal FP64/bf16 1.25/2250 "
+                           "(GB300 FP64 FMA and FP64 mma.sync rates are equal)",
+            "traffic": (tr["dram_bytes"] if tr else None),
+            "traffic_launch": (tr["launch"] if tr else None),
+            "launches_per_step": g_n / len(infos), "ms_per_step": g_ms / len(infos),
+            "share_of_step": (g_ms / len(infos)) / ms}
+    symv = {"kernel": "k_symv_cols_v2 (ke1)", "launches_per_step": s_n / len(infos),
+            "ms_per_launch": s_ms / max(1, s_n), "achieved_gbs": s_by / (s_ms * 1e-3) / 1e9 if s_ms else 0.0,
+            "frac_hbm": (s_by / (s_ms * 1e-3) / 1e9) / peaks.get("hbm_gbs", HBM_GBS) if s_ms else 0.0,
+            "achieved_tflops": s_fl / (s_ms * 1e-3) / 1e12 if s_ms else 0.0, "share_of_step": (s_ms / len(infos)) / ms}
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": ms_all / 1e3, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": n, "s": s, "which": "smallest", "krylov_dim": last["krylov_dim"],
+                   "keep": last["keep"], "tol": 1e-12, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (2 x %.1f GB vs 129 MB)" % (n * n * 8 / 1e9)},
+        "stages_ms": {k: last[k] for k in ("ms_gs1", "ms_gs2", "ms_ke", "ms_ke3", "ms_bt1", "ms_total")},
+        "lanczos": {"matvecs": last["matvecs"], "restarts": last["restarts"], "nconv": last["nconv"]},
+        "accuracy": {"max_rel_eig_err_vs_constructed": rel, "max_eta": eta, "orth_err": orth},
+        "roofline": roof, "symv": symv,
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * s + s) * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if args.gpus == 1 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(n, s, args.cpu_sample_n)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _power(M, iters=30):
+    import torch
+
+    g = torch.Generator(device=M.device).manual_seed(0)
+    v = torch.randn(M.shape[0], device=M.device, dtype=M.dtype, generator=g)
+    v /= v.norm()
+    lam = 0.0
+    for _ in range(iters):
+        w = M @ v
+        lam = float(w.norm())
+        v = w / lam
+    return lam
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--s", type=int, default=100)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-n", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.workload = f"gsyeig n={args.n} s={args.s} smallest, FP64, known-spectrum synthetic pencil"
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,161 @@
+/*
+ * gsyeig — a few eigenpairs of the dense symmetric-definite generalized
+ * eigenproblem  A X = B X Lambda  on one NVIDIA GB300 (sm_103a).
+ *
+ * Paper: Aliaga, Bientinesi, Davidovic, Di Napoli, Igual, Quintana-Orti,
+ * "Solving Dense Generalized Eigenproblems on Multi-threaded Architectures"
+ * (arXiv 1111.6374).  The route is the paper's Krylov variant KE
+ * (Section 2.3, Table 1):
+ *
+ *   gs1  B = U^T U                      Cholesky, U upper          (Eq. 2)
+ *   gs2  C = U^-T A U^-1                explicit standard form     (Eq. 3)
+ *   ke1  z = C w                        symmetric matrix-vector product
+ *   ke2  Lanczos recurrence with full reorthogonalisation ("twice is
+ *        enough") and implicit restarts (QR iteration on T_m)
+ *   ke3  Ritz pairs of the tridiagonal T_m, Y = V_m S
+ *   bt1  X = U^-1 Y                     back-transform              (Eq. 4)
+ *
+ * Conventions for every entry point below
+ *  - Matrices are double precision, column-major, element (i, j) at
+ *    M[i + j*ld], with ld >= n.  A symmetric matrix stored full is the same
+ *    in row- and column-major order.
+ *  - Unless stated otherwise pointers are DEVICE pointers owned by the
+ *    caller; the library never frees them.  gsyeig_solve also accepts host
+ *    pointers (see there).
+ *  - Every call is synchronous on return.  Work is issued on the handle's
+ *    own stream, ordered after the work already queued on the stream given
+ *    to gsyeig_create (NULL = the legacy default stream).
+ *  - Return value: GSYEIG_SUCCESS (0); -i when argument i (1-based) is
+ *    invalid; or one of the positive status codes below.  Nothing is
+ *    written to outputs when an argument is invalid.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef GSYEIG_H
+#define GSYEIG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsyeig_ctx *gsyeig_handle;
+
+typedef enum { GSYEIG_SMALLEST = 0, GSYEIG_LARGEST = 1 } gsyeig_which;
+
+enum {
+  GSYEIG_SUCCESS = 0,
+  GSYEIG_NOT_SPD = 1,        /* Cholesky of B met a non-positive pivot (Eq. 2); see info.potrf_index */
+  GSYEIG_NO_CONVERGENCE = 2, /* max_restarts reached with fewer than s converged pairs; best pairs returned */
+  GSYEIG_TIMEOUT = 3,        /* the wall-clock budget opts.timeout_ms ran out between restarts */
+  GSYEIG_CUDA_ERROR = 4,     /* a CUDA runtime call failed; the handle should be destroyed */
+  GSYEIG_OOM = 5,            /* device workspace could not be allocated */
+  GSYEIG_NOT_SUPPORTED = 6   /* option combination not available */
+};
+
+/* Solver options (gsyeig_default_options fills the defaults). */
+typedef struct {
+  double tol;           /* accept Ritz pair i when |beta_m s_{m,i}| <= tol * max|theta| (default 1e-12) */
+  int64_t krylov_dim;   /* m, Lanczos basis size, s < m <= n; 0 = min(n, max(3s, s + 16)) */
+  int64_t keep;         /* k, vectors kept at a restart, s <= k < m; 0 = min(s + max(2, s/4), m - 1) */
+  int64_t max_restarts; /* default 2000 */
+  uint64_t seed;        /* seed of the counter-based start vector (default 0) */
+  const double *v0;     /* optional device start vector of length n (NULL = random) */
+  double timeout_ms;    /* 0 = none; checked between restarts only */
+  int32_t block;        /* panel width nb of the blocked factorisations, 16..160; 0 = default (64) */
+  int32_t profile;      /* 1 = time every GEMM-engine and symv launch with CUDA events on the
+                           library stream and report them in gsyeig_info (small overhead) */
+} gsyeig_opts;
+
+/* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
+ * (Table 2 / Table 6: gs1, gs2, ke1+ke2, ke3, bt1). */
+typedef struct {
+  int64_t n, s;
+  int64_t nconv;        /* wanted pairs whose Ritz estimate met tol */
+  int64_t restarts;     /* implicit restarts performed */
+  int64_t matvecs;      /* applications of C (ke1) */
+  int64_t krylov_dim, keep;
+  int64_t potrf_index;  /* 1-based failing pivot when GSYEIG_NOT_SPD, else 0 */
+  int64_t breakdowns;   /* Lanczos breakdowns recovered by a fresh random vector */
+  int64_t kernel_launches; /* kernels launched by this call (graph nodes included) */
+  double ms_gs1, ms_gs2, ms_ke, ms_ke3, ms_bt1, ms_total;
+  double max_ritz_estimate; /* max over wanted pairs of |beta_m s_{m,i}| / max|theta| */
+  /* opts.profile = 1: per kernel class (GEMM engine of gs1/gs2/bt1/restarts; symv of ke1)
+   * the launches, summed CUDA-event time, and the algorithmic flops and bytes of those launches */
+  int64_t gemm_launches, symv_launches;
+  double gemm_ms, gemm_flops, gemm_bytes;
+  double symv_ms, symv_flops, symv_bytes;
+} gsyeig_info;
+
+/* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * (NULL = legacy default stream) that all calls order themselves after. */
+int gsyeig_create(gsyeig_handle *h, int device, void *cuda_stream);
+
+/* Release the handle and its device workspace. */
+int gsyeig_destroy(gsyeig_handle h);
+
+/* Fill *o with the defaults. */
+int gsyeig_default_options(gsyeig_opts *o);
+
+/* Copy *o into the handle (validated: tol > 0, keep < krylov_dim, ...). */
+int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o);
+
+/* Human-readable text for a status code. */
+const char *gsyeig_strerror(int status);
+
+/*
+ * The whole KE route (Section 2.3) for the s smallest (which = SMALLEST) or
+ * largest eigenpairs of (A, B), 1 <= s < n.
+ *  dA (n x n, lda): on entry the symmetric A, lower triangle read; on exit
+ *      C = U^-T A U^-1 stored full (Eq. 3: "the entries of A can be
+ *      overwritten with the result C").
+ *  dB (n x n, ldb): on entry the SPD B, upper triangle read; on exit U in
+ *      the upper triangle (Eq. 2); the strictly lower triangle is not touched.
+ *  w  (s): eigenvalues in ascending order.  Host or device pointer.
+ *  dX (n x s, ldx): B-orthonormal eigenvectors, column i for w[i].
+ *  info: may be NULL.
+ * If dA and dB are HOST pointers the library copies them to its own device
+ * workspace, leaves the host arrays unchanged, and dX must then be a host
+ * pointer too (the result is copied back).  Returns GSYEIG_NOT_SPD,
+ * GSYEIG_NO_CONVERGENCE (best pairs still written), GSYEIG_TIMEOUT, ...
+ */
+int gsyeig_solve(gsyeig_handle h, double *dA, int64_t lda, double *dB, int64_t ldb, int64_t n, int64_t s,
+                 int which, double *w, double *dX, int64_t ldx, gsyeig_info *info);
+
+/* ---- single steps of the route, device pointers only ------------------ */
+
+/* gs1 (Eq. 2): B = U^T U, U written over the upper triangle of dB; strictly
+ * lower triangle untouched.  *potrf_index (host, may be NULL) gets 0 or the
+ * 1-based index of the first non-positive pivot (then GSYEIG_NOT_SPD). */
+int gsyeig_potrf(gsyeig_handle h, double *dB, int64_t ldb, int64_t n, int64_t *potrf_index);
+
+/* gs2 (Eq. 3): C = U^-T A U^-1 over dA (lower triangle of A read, C written
+ * full), U the upper triangle of dU. */
+int gsyeig_sygst(gsyeig_handle h, double *dA, int64_t lda, const double *dU, int64_t ldu, int64_t n);
+
+/* ke1: z = C w for the full symmetric n x n dC (both triangles read). */
+int gsyeig_symv(gsyeig_handle h, const double *dC, int64_t ldc, int64_t n, const double *dw, double *dz);
+
+/* bt1 (Eq. 4): Y <- U^-1 Y in place on the n x s block dY. */
+int gsyeig_trsm_back(gsyeig_handle h, const double *dU, int64_t ldu, int64_t n, double *dY, int64_t ldy, int64_t s);
+
+/* Stage (2) of KE alone: s eigenpairs of the full symmetric dC by
+ * implicitly restarted Lanczos.  w (host or device, ascending), dY (n x s,
+ * orthonormal columns).  dC is read only. */
+int gsyeig_syev_lanczos(gsyeig_handle h, const double *dC, int64_t ldc, int64_t n, int64_t s, int which,
+                        double *w, double *dY, int64_t ldy, gsyeig_info *info);
+
+/* ke3 building block: eigenvalues lam[0..cnt-1] with indices first..first+cnt-1
+ * (ascending order, 0-based) of the symmetric tridiagonal (d[0..m-1],
+ * e[0..m-2]) by Sturm-count bisection, and, if dZ != NULL, unit eigenvectors
+ * by inverse iteration (m x cnt, ldz).  All pointers device. */
+int gsyeig_tridiag_eig(gsyeig_handle h, const double *d, const double *e, int64_t m, int64_t first, int64_t cnt,
+                       double *lam, double *dZ, int64_t ldz);
+
+/* Number of kernels this library has launched in the calling process. */
+int64_t gsyeig_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSYEIG_H */

@@ -1,0 +1,132 @@
+// Shared definitions for the GB300 (sm_103a) gsyeig library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstddef>
+#include <vector>
+
+#include "gsyeig.h"
+
+#define GS_IDX(i, j, ld) ((size_t)(i) + (size_t)(j) * (size_t)(ld))
+
+namespace gs {
+
+// Process-wide count of kernels issued by this library (graph nodes counted
+// when the graph is launched).
+extern std::atomic<int64_t> g_launches;
+
+inline void count_launch(int64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Status carried through the host-side drivers.
+struct Status {
+  int code = GSYEIG_SUCCESS;
+  explicit operator bool() const { return code == GSYEIG_SUCCESS; }
+};
+
+#define GS_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) {                               \
+      last_cuda_error() = _e;                              \
+      return _e == cudaErrorMemoryAllocation ? GSYEIG_OOM  \
+                                             : GSYEIG_CUDA_ERROR; \
+    }                                                      \
+  } while (0)
+
+#define GS_CHECK_LAUNCH()                                  \
+  do {                                                     \
+    cudaError_t _e = cudaGetLastError();                   \
+    if (_e != cudaSuccess) {                               \
+      last_cuda_error() = _e;                              \
+      return GSYEIG_CUDA_ERROR;                            \
+    }                                                      \
+  } while (0)
+
+#define GS_TRY(expr)                  \
+  do {                                \
+    int _st = (expr);                 \
+    if (_st != GSYEIG_SUCCESS) return _st; \
+  } while (0)
+
+cudaError_t &last_cuda_error();
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------------------
+// Optional per-launch timing (opts.profile): CUDA events recorded on the
+// launching stream around each GEMM-engine / symv launch, resolved after the
+// call has synchronised.  One profiler per handle, installed for the
+// duration of an API call on the calling thread.
+// ---------------------------------------------------------------------------
+enum ProfClass { PROF_GEMM = 0, PROF_SYMV = 1, PROF_NCLASS = 2 };
+
+struct KernelProfiler {
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec {
+    int cls;
+    double flops, bytes;
+    size_t e0;
+  };
+  std::vector<Rec> recs;
+  // start: returns the index of the start event (or SIZE_MAX on failure)
+  size_t start(cudaStream_t st);
+  void stop(cudaStream_t st, size_t e0, int cls, double flops, double bytes);
+  // after synchronisation: per-class launches, ms, flops, bytes; then reset
+  void resolve(int64_t launches[PROF_NCLASS], double ms[PROF_NCLASS], double flops[PROF_NCLASS],
+               double bytes[PROF_NCLASS]);
+  void release();
+};
+
+KernelProfiler *&current_profiler();
+
+// ---------------------------------------------------------------------------
+// GEMM engine (FP64):  C = alpha * op(A) * op(B) + beta * C on an M x N
+// column-major block, op(X) = X or X^T.  `mode` restricts which elements
+// of C are written: ALL, LOWER (i - j + diag >= 0) or UPPER (i - j + diag
+// <= 0), with i, j the row/column inside the block; tiles wholly outside
+// the region are skipped.  If abort_flag != nullptr and *abort_flag != 0
+// the kernel returns without work (used to stop a factorisation after a
+// failed pivot without a host round trip).
+// ---------------------------------------------------------------------------
+enum TriMode { TRI_ALL = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+
+int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
+          const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+          TriMode mode = TRI_ALL, int64_t diag = 0, const int *abort_flag = nullptr);
+
+// Copy an M x N block (column-major, both with leading dimensions).
+int copy_block(cudaStream_t st, int64_t M, int64_t N, const double *src, int64_t lds, double *dst, int64_t ldd,
+               const int *abort_flag = nullptr);
+
+// Mirror one triangle of an n x n matrix into the other: lower_to_upper
+// copies A[i][j] (i > j) to A[j][i]; otherwise the reverse.
+int symmetrize(cudaStream_t st, int64_t n, double *A, int64_t lda, bool lower_to_upper);
+
+// ---------------------------------------------------------------------------
+// Dense factorisation drivers (factor.cu).
+// ---------------------------------------------------------------------------
+struct FactorWork {
+  double *Uinv = nullptr;   // inverses of the nb x nb diagonal blocks of U, (nb x nb) each, ld nb
+  double *panel = nullptr;  // staging buffer, max(nb, ...) x n
+  size_t panel_elems = 0;
+  int *flag = nullptr;      // device int: first failed pivot (1-based) or 0
+};
+
+int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, FactorWork &w);
+int trtri_diag_blocks(cudaStream_t st, int64_t n, const double *U, int64_t ldu, int nb, double *Uinv);
+int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *U, int64_t ldu, int nb,
+                  FactorWork &w, bool have_uinv);
+int trsm_back_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu, double *Y, int64_t ldy, int64_t s,
+                      int nb, FactorWork &w, bool have_uinv);
+
+// ---------------------------------------------------------------------------
+// Operator application (symv.cu): z = C w, C full symmetric.
+// ---------------------------------------------------------------------------
+int symv_f64(cudaStream_t st, int64_t n, const double *C, int64_t ldc, const double *w, double *z);
+
+}  // namespace gs

@@ -1,0 +1,584 @@
+// C ABI of the library and the host-side driver of the KE route
+// (Section 2.3 of the paper; Table 1 keys gs1, gs2, ke1-ke3, bt1).
+// Device memory for inputs/outputs belongs to the caller; the handle owns a
+// grow-on-demand workspace.  The driver only sequences kernels and reads
+// back a few scalars per restart (converged count, breakdown flag).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "lanczos.cuh"
+
+namespace gs {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t need) {
+    if (need <= bytes) return GSYEIG_SUCCESS;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return GSYEIG_OOM;
+    }
+    bytes = need;
+    return GSYEIG_SUCCESS;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  double *d() const { return static_cast<double *>(p); }
+};
+
+}  // namespace gs
+
+using namespace gs;
+
+struct gsyeig_ctx {
+  int device = 0;
+  cudaStream_t user = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev[10] = {};  // 0-6 stage marks, 8 end mark, 9 user-stream ordering
+  gsyeig_opts opts{};
+  // workspace
+  DevBuf uinv, panel, flag;
+  DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts;
+  DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
+  KernelProfiler prof;
+};
+
+namespace {
+
+constexpr int kDefaultBlock = 64;
+
+// Installs the handle's profiler for the duration of one API call when
+// opts.profile is set; fills the profile fields of info on request.
+struct ProfScope {
+  gsyeig_handle h;
+  bool on;
+  explicit ProfScope(gsyeig_handle hh) : h(hh), on(hh->opts.profile != 0) {
+    if (on) current_profiler() = &h->prof;
+  }
+  void fill(gsyeig_info *info) {
+    if (!on) return;
+    int64_t l[PROF_NCLASS];
+    double ms[PROF_NCLASS], fl[PROF_NCLASS], by[PROF_NCLASS];
+    h->prof.resolve(l, ms, fl, by);
+    if (!info) return;
+    info->gemm_launches = l[PROF_GEMM];
+    info->gemm_ms = ms[PROF_GEMM];
+    info->gemm_flops = fl[PROF_GEMM];
+    info->gemm_bytes = by[PROF_GEMM];
+    info->symv_launches = l[PROF_SYMV];
+    info->symv_ms = ms[PROF_SYMV];
+    info->symv_flops = fl[PROF_SYMV];
+    info->symv_bytes = by[PROF_SYMV];
+  }
+  ~ProfScope() {
+    if (on) {
+      current_profiler() = nullptr;
+      h->prof.recs.clear();
+      h->prof.used = 0;
+    }
+  }
+};
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int begin(gsyeig_handle h) {
+  GS_CUDA(cudaSetDevice(h->device));
+  GS_CUDA(cudaEventRecord(h->ev[9], h->user));
+  GS_CUDA(cudaStreamWaitEvent(h->st, h->ev[9], 0));
+  return GSYEIG_SUCCESS;
+}
+
+int finish(gsyeig_handle h) {
+  GS_CUDA(cudaStreamSynchronize(h->st));
+  GS_CUDA(cudaGetLastError());
+  return GSYEIG_SUCCESS;
+}
+
+int nb_of(gsyeig_handle h, int64_t n) {
+  int nb = h->opts.block > 0 ? h->opts.block : kDefaultBlock;
+  if (nb > n) nb = (int)std::max<int64_t>(1, n);
+  return nb;
+}
+
+int factor_ws(gsyeig_handle h, int64_t n, int nb, int64_t s, FactorWork &w) {
+  const int64_t nblk = ceil_div(n, nb);
+  GS_TRY(h->uinv.ensure((size_t)nblk * nb * nb * sizeof(double)));
+  GS_TRY(h->panel.ensure((size_t)std::max<int64_t>(n, s) * nb * sizeof(double) + 64));
+  GS_TRY(h->flag.ensure(64));
+  w.Uinv = h->uinv.d();
+  w.panel = h->panel.d();
+  w.flag = static_cast<int *>(h->flag.p);
+  return GSYEIG_SUCCESS;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.f;
+  }
+  return ms;
+}
+
+struct LanczosParams {
+  int64_t m, k;
+};
+
+LanczosParams lanczos_params(const gsyeig_opts &o, int64_t n, int64_t s) {
+  int64_t m = o.krylov_dim > 0 ? o.krylov_dim : std::min<int64_t>(n, std::max<int64_t>(3 * s, s + 16));
+  m = std::min<int64_t>(m, n);
+  int64_t k = o.keep > 0 ? o.keep : std::min<int64_t>(s + std::max<int64_t>(2, s / 4), m - 1);
+  return {m, k};
+}
+
+// One Lanczos step j: z = C v_j, CGS2 against v_0..v_j, alpha_j, beta_j, v_{j+1}.
+int lanczos_step(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t m, int64_t j, const double *C, int64_t ldc) {
+  double *V = h->V.d(), *z = h->z.d();
+  GS_TRY(symv_f64(st, n, C, ldc, V + (size_t)j * n, z));
+  GS_TRY(lz_cgs2(st, n, j + 1, V, n, z, h->h1.d(), h->h2.d(), h->sq.d()));
+  GS_TRY(lz_finalize(st, j, m, h->h1.d(), h->h2.d(), h->sq.d(), lz_nparts(n), h->alpha.d(), h->beta.d(),
+                     static_cast<LanczosState *>(h->state.p)));
+  GS_TRY(lz_scale_into(st, n, z, V + (size_t)(j + 1) * n, static_cast<LanczosState *>(h->state.p)));
+  return GSYEIG_SUCCESS;
+}
+
+// Put a fresh random unit vector, orthogonal to V[:, 0:ncols], in V[:, ncols].
+int fresh_vector(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t ncols, uint64_t stream_id, double *norm_out) {
+  double *V = h->V.d(), *z = h->z.d();
+  LanczosState *state = static_cast<LanczosState *>(h->state.p);
+  GS_TRY(lz_random(st, n, h->opts.seed, stream_id, z));
+  GS_TRY(lz_cgs2(st, n, ncols, V, n, z, h->h1.d(), h->h2.d(), h->sq.d()));
+  GS_TRY(lz_norm_finish(st, h->sq.d(), lz_nparts(n), state, norm_out));
+  GS_TRY(lz_scale_into(st, n, z, V + (size_t)ncols * n, state));
+  return GSYEIG_SUCCESS;
+}
+
+// Implicitly restarted Lanczos on the full symmetric C (ke1, ke2, ke3).
+// Output: the s wanted Ritz values (ascending) in theta_out (device) and
+// Ritz vectors in Y (n x s, ld ldy, device).
+int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_t s, int which, double *theta_out,
+                double *Y, int64_t ldy, gsyeig_info *info, double *ms_ke3) {
+  cudaStream_t st = h->st;
+  const LanczosParams P = lanczos_params(h->opts, n, s);
+  const int64_t m = P.m, k = P.k, p = m - k;
+  if (!(s <= k && k < m && m <= n)) return GSYEIG_NOT_SUPPORTED;
+  const int64_t np = lz_nparts(n);
+  GS_TRY(h->V.ensure((size_t)n * (m + 1) * sizeof(double)));
+  GS_TRY(h->Vq.ensure((size_t)n * (k + 1) * sizeof(double)));
+  GS_TRY(h->z.ensure((size_t)n * sizeof(double)));
+  GS_TRY(h->h1.ensure((size_t)(m + 1) * sizeof(double)));
+  GS_TRY(h->h2.ensure((size_t)(m + 1) * sizeof(double)));
+  GS_TRY(h->sq.ensure((size_t)(np + 1) * sizeof(double)));
+  GS_TRY(h->alpha.ensure((size_t)m * sizeof(double)));
+  GS_TRY(h->beta.ensure((size_t)m * sizeof(double)));
+  GS_TRY(h->alphaP.ensure((size_t)m * sizeof(double)));
+  GS_TRY(h->betaP.ensure((size_t)m * sizeof(double)));
+  GS_TRY(h->theta.ensure((size_t)m * sizeof(double)));
+  GS_TRY(h->S.ensure((size_t)m * s * sizeof(double)));
+  GS_TRY(h->Q.ensure((size_t)m * m * sizeof(double)));
+  GS_TRY(h->rot.ensure((size_t)2 * std::max<int64_t>(p, 1) * (m - 1 + 1) * sizeof(double)));
+  GS_TRY(h->invw.ensure((size_t)5 * m * s * sizeof(double)));
+  GS_TRY(h->state.ensure(sizeof(LanczosState)));
+  double *V = h->V.d();
+  LanczosState *dstate = static_cast<LanczosState *>(h->state.p);
+  LanczosState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.breakdown_at = -1;
+  GS_CUDA(cudaMemcpyAsync(dstate, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+  GS_CUDA(cudaMemsetAsync(h->beta.p, 0, (size_t)m * sizeof(double), st));
+
+  // v_0: the caller's start vector or a counter-based random one, normalised
+  if (h->opts.v0) GS_CUDA(cudaMemcpyAsync(h->z.p, h->opts.v0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else GS_TRY(lz_random(st, n, h->opts.seed, 0, h->z.d()));
+  GS_TRY(lz_cgs2(st, n, 0, V, n, h->z.d(), h->h1.d(), h->h2.d(), h->sq.d()));
+  GS_TRY(lz_norm_finish(st, h->sq.d(), (int)np, dstate, nullptr));
+  GS_TRY(lz_scale_into(st, n, h->z.d(), V, dstate));
+
+  const int64_t wf = (which == GSYEIG_LARGEST) ? m - s : 0;  // first wanted index among the m Ritz values
+  const double *shifts = (which == GSYEIG_LARGEST) ? h->theta.d() : h->theta.d() + k;
+  const int dir = (which == GSYEIG_LARGEST) ? -1 : 1;  // nearest-to-wanted shift first
+  int64_t j0 = 0, restarts = 0, matvecs = 0, breakdowns = 0;
+  int status = GSYEIG_SUCCESS;
+  auto t_start = std::chrono::steady_clock::now();
+  for (;;) {
+    for (int64_t j = j0; j < m; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
+    matvecs += m - j0;
+    GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (hs.breakdown_at >= 0 && hs.breakdown_at < m - 1) {
+      // invariant subspace met: continue from a fresh random direction
+      const int64_t b = hs.breakdown_at;
+      breakdowns++;
+      hs.breakdown_at = -1;
+      GS_CUDA(cudaMemcpyAsync(&dstate->breakdown_at, &hs.breakdown_at, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+      GS_TRY(fresh_vector(h, st, n, b + 1, 1000 + (uint64_t)breakdowns, nullptr));
+      j0 = b + 1;
+      if (breakdowns > m) return GSYEIG_NO_CONVERGENCE;
+      continue;
+    }
+    // Ritz values of T_m, vectors of the wanted ones, convergence test
+    GS_TRY(tri_bisect(st, m, h->alpha.d(), h->beta.d(), 0, m, h->theta.d()));
+    GS_TRY(tri_invit(st, m, h->alpha.d(), h->beta.d(), s, h->theta.d() + wf, h->S.d(), m, h->invw.d()));
+    GS_TRY(tri_converged(st, m, s, h->theta.d(), h->beta.d(), h->S.d(), m, h->opts.tol, dstate));
+    GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (hs.nconv >= s) break;
+    if (restarts >= h->opts.max_restarts) {
+      status = GSYEIG_NO_CONVERGENCE;
+      break;
+    }
+    if (h->opts.timeout_ms > 0) {
+      double el = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+      if (el > h->opts.timeout_ms) {
+        status = GSYEIG_TIMEOUT;
+        break;
+      }
+    }
+    // implicit restart with the p unwanted Ritz values as exact shifts
+    GS_TRY(tri_qr_shifts(st, m, p, h->alpha.d(), h->beta.d(), shifts, dir, h->alphaP.d(), h->betaP.d(), h->Q.d(), m,
+                         h->rot.d()));
+    GS_TRY(dgemm(st, false, false, n, k + 1, m, 1.0, V, n, h->Q.d(), m, 0.0, h->Vq.d(), n));
+    GS_TRY(lz_restart_residual(st, n, k, m, h->Vq.d(), n, V + (size_t)m * n, h->betaP.d(), h->beta.d(), h->Q.d(), m,
+                               h->z.d()));
+    GS_TRY(copy_block(st, n, k, h->Vq.d(), n, V, n));
+    GS_CUDA(cudaMemcpyAsync(h->alpha.p, h->alphaP.p, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(h->beta.p, h->betaP.p, (size_t)(k - 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemsetAsync(h->beta.d() + k, 0, (size_t)(m - k) * sizeof(double), st));
+    // clean the new residual against V_k (CGS2), beta_{k-1} = ||f||, v_k = f / ||f||
+    GS_TRY(lz_cgs2(st, n, k, V, n, h->z.d(), h->h1.d(), h->h2.d(), h->sq.d()));
+    GS_TRY(lz_norm_finish(st, h->sq.d(), (int)np, dstate, h->beta.d() + (k - 1)));
+    GS_TRY(lz_scale_into(st, n, h->z.d(), V + (size_t)k * n, dstate));
+    restarts++;
+    j0 = k;
+  }
+  // ke3: Ritz vectors Y = V_m S
+  cudaEvent_t e0 = h->ev[5], e1 = h->ev[6];
+  GS_CUDA(cudaEventRecord(e0, st));
+  GS_TRY(dgemm(st, false, false, n, s, m, 1.0, V, n, h->S.d(), m, 0.0, Y, ldy));
+  GS_CUDA(cudaMemcpyAsync(theta_out, h->theta.d() + wf, (size_t)s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  GS_CUDA(cudaEventRecord(e1, st));
+  GS_CUDA(cudaEventSynchronize(e1));
+  if (ms_ke3) *ms_ke3 = elapsed(e0, e1);
+  if (info) {
+    info->nconv = hs.nconv;
+    info->restarts = restarts;
+    info->matvecs = matvecs;
+    info->krylov_dim = m;
+    info->keep = k;
+    info->breakdowns = breakdowns;
+    info->max_ritz_estimate = hs.max_est;
+  }
+  return status;
+}
+
+int check_solve_args(int64_t lda, int64_t ldb, int64_t n, int64_t s, int which, const void *A, const void *B,
+                     const void *w, const void *X, int64_t ldx) {
+  if (!A) return -2;
+  if (lda < std::max<int64_t>(1, n)) return -3;
+  if (!B) return -4;
+  if (ldb < std::max<int64_t>(1, n)) return -5;
+  if (n < 2) return -6;
+  if (s < 1 || s >= n) return -7;
+  if (which != GSYEIG_SMALLEST && which != GSYEIG_LARGEST) return -8;
+  if (!w) return -9;
+  if (!X) return -10;
+  if (ldx < n) return -11;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsyeig_default_options(gsyeig_opts *o) {
+  if (!o) return -1;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-12;
+  o->max_restarts = 2000;
+  return GSYEIG_SUCCESS;
+}
+
+int gsyeig_create(gsyeig_handle *hp, int device, void *cuda_stream) {
+  if (!hp) return -1;
+  *hp = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return GSYEIG_CUDA_ERROR;
+  }
+  if (device < 0 || device >= ndev) return -2;
+  gsyeig_ctx *h = new (std::nothrow) gsyeig_ctx();
+  if (!h) return GSYEIG_OOM;
+  h->device = device;
+  h->user = static_cast<cudaStream_t>(cuda_stream);
+  gsyeig_default_options(&h->opts);
+  if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return GSYEIG_CUDA_ERROR;
+  }
+  for (auto &e : h->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      gsyeig_destroy(h);
+      return GSYEIG_CUDA_ERROR;
+    }
+  *hp = h;
+  return GSYEIG_SUCCESS;
+}
+
+int gsyeig_destroy(gsyeig_handle h) {
+  if (!h) return -1;
+  cudaSetDevice(h->device);
+  if (h->st) cudaStreamSynchronize(h->st);
+  DevBuf *bufs[] = {&h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
+                    &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
+                    &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
+  for (DevBuf *b : bufs) b->release();
+  h->prof.release();
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->st) cudaStreamDestroy(h->st);
+  delete h;
+  return GSYEIG_SUCCESS;
+}
+
+int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
+  if (!h) return -1;
+  if (!o) return -2;
+  if (!(o->tol > 0.0) || o->krylov_dim < 0 || o->keep < 0 || o->max_restarts < 0 || o->timeout_ms < 0 ||
+      o->block < 0 || o->block > 160 || (o->block > 0 && o->block < 16) || o->profile < 0 || o->profile > 1)
+    return -2;
+  if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
+  h->opts = *o;
+  return GSYEIG_SUCCESS;
+}
+
+const char *gsyeig_strerror(int status) {
+  switch (status) {
+    case GSYEIG_SUCCESS: return "success";
+    case GSYEIG_NOT_SPD: return "B is not positive definite (Cholesky pivot <= 0)";
+    case GSYEIG_NO_CONVERGENCE: return "Lanczos did not converge within max_restarts";
+    case GSYEIG_TIMEOUT: return "time budget exhausted";
+    case GSYEIG_CUDA_ERROR: return "CUDA runtime error";
+    case GSYEIG_OOM: return "out of device memory";
+    case GSYEIG_NOT_SUPPORTED: return "unsupported parameter combination";
+    default: return status < 0 ? "invalid argument" : "unknown status";
+  }
+}
+
+int64_t gsyeig_kernel_launches(void) { return g_launches.load(); }
+
+int gsyeig_potrf(gsyeig_handle h, double *dB, int64_t ldb, int64_t n, int64_t *potrf_index) {
+  if (!h) return -1;
+  if (!dB) return -2;
+  if (ldb < std::max<int64_t>(1, n)) return -3;
+  if (n < 1) return -4;
+  GS_TRY(begin(h));
+  const int nb = nb_of(h, n);
+  FactorWork w;
+  GS_TRY(factor_ws(h, n, nb, 1, w));
+  GS_TRY(potrf_blocked(h->st, n, dB, ldb, nb, w));
+  int flag = 0;
+  GS_CUDA(cudaMemcpyAsync(&flag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  GS_TRY(finish(h));
+  if (potrf_index) *potrf_index = flag;
+  return flag ? GSYEIG_NOT_SPD : GSYEIG_SUCCESS;
+}
+
+int gsyeig_sygst(gsyeig_handle h, double *dA, int64_t lda, const double *dU, int64_t ldu, int64_t n) {
+  if (!h) return -1;
+  if (!dA) return -2;
+  if (lda < std::max<int64_t>(1, n)) return -3;
+  if (!dU) return -4;
+  if (ldu < std::max<int64_t>(1, n)) return -5;
+  if (n < 1) return -6;
+  GS_TRY(begin(h));
+  const int nb = nb_of(h, n);
+  FactorWork w;
+  GS_TRY(factor_ws(h, n, nb, 1, w));
+  GS_TRY(sygst_blocked(h->st, n, dA, lda, dU, ldu, nb, w, false));
+  return finish(h);
+}
+
+int gsyeig_symv(gsyeig_handle h, const double *dC, int64_t ldc, int64_t n, const double *dw, double *dz) {
+  if (!h) return -1;
+  if (!dC) return -2;
+  if (ldc < std::max<int64_t>(1, n)) return -3;
+  if (n < 1) return -4;
+  if (!dw) return -5;
+  if (!dz) return -6;
+  GS_TRY(begin(h));
+  GS_TRY(symv_f64(h->st, n, dC, ldc, dw, dz));
+  return finish(h);
+}
+
+int gsyeig_trsm_back(gsyeig_handle h, const double *dU, int64_t ldu, int64_t n, double *dY, int64_t ldy, int64_t s) {
+  if (!h) return -1;
+  if (!dU) return -2;
+  if (ldu < std::max<int64_t>(1, n)) return -3;
+  if (n < 1) return -4;
+  if (!dY) return -5;
+  if (ldy < n) return -6;
+  if (s < 1) return -7;
+  GS_TRY(begin(h));
+  const int nb = nb_of(h, n);
+  FactorWork w;
+  GS_TRY(factor_ws(h, n, nb, s, w));
+  GS_TRY(trsm_back_blocked(h->st, n, dU, ldu, dY, ldy, s, nb, w, false));
+  return finish(h);
+}
+
+int gsyeig_tridiag_eig(gsyeig_handle h, const double *d, const double *e, int64_t m, int64_t first, int64_t cnt,
+                       double *lam, double *dZ, int64_t ldz) {
+  if (!h) return -1;
+  if (!d) return -2;
+  if (!e && m > 1) return -3;
+  if (m < 1) return -4;
+  if (first < 0 || first >= m) return -5;
+  if (cnt < 1 || first + cnt > m) return -6;
+  if (!lam) return -7;
+  if (dZ && ldz < m) return -9;
+  GS_TRY(begin(h));
+  GS_TRY(tri_bisect(h->st, m, d, e, first, cnt, lam));
+  if (dZ) {
+    GS_TRY(h->invw.ensure((size_t)5 * m * cnt * sizeof(double)));
+    GS_TRY(tri_invit(h->st, m, d, e, cnt, lam, dZ, ldz, h->invw.d()));
+  }
+  return finish(h);
+}
+
+int gsyeig_syev_lanczos(gsyeig_handle h, const double *dC, int64_t ldc, int64_t n, int64_t s, int which, double *w,
+                        double *dY, int64_t ldy, gsyeig_info *info) {
+  if (!h) return -1;
+  if (!dC) return -2;
+  if (ldc < std::max<int64_t>(1, n)) return -3;
+  if (n < 2) return -4;
+  if (s < 1 || s >= n) return -5;
+  if (which != GSYEIG_SMALLEST && which != GSYEIG_LARGEST) return -6;
+  if (!w) return -7;
+  if (!dY) return -8;
+  if (ldy < n) return -9;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->n = n;
+    info->s = s;
+  }
+  const int64_t l0 = g_launches.load();
+  GS_TRY(begin(h));
+  ProfScope prof(h);
+  GS_TRY(h->hw.ensure((size_t)s * sizeof(double)));
+  double ms_ke3 = 0;
+  cudaEventRecord(h->ev[0], h->st);
+  int st = lanczos_run(h, dC, ldc, n, s, which, h->hw.d(), dY, ldy, info, &ms_ke3);
+  if (st != GSYEIG_SUCCESS && st != GSYEIG_NO_CONVERGENCE && st != GSYEIG_TIMEOUT) return st;
+  GS_CUDA(cudaMemcpyAsync(w, h->hw.p, (size_t)s * sizeof(double), cudaMemcpyDefault, h->st));
+  cudaEventRecord(h->ev[1], h->st);
+  GS_TRY(finish(h));
+  prof.fill(info);
+  if (info) {
+    info->ms_ke = elapsed(h->ev[0], h->ev[1]) - ms_ke3;
+    info->ms_ke3 = ms_ke3;
+    info->ms_total = elapsed(h->ev[0], h->ev[1]);
+    info->kernel_launches = g_launches.load() - l0;
+  }
+  return st;
+}
+
+int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb, int64_t n, int64_t s, int which,
+                 double *w, double *X, int64_t ldx, gsyeig_info *info) {
+  if (!h) return -1;
+  int bad = check_solve_args(lda, ldb, n, s, which, A, B, w, X, ldx);
+  if (bad) return bad;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->n = n;
+    info->s = s;
+  }
+  const int64_t l0 = g_launches.load();
+  GS_TRY(begin(h));
+  ProfScope prof(h);
+  cudaStream_t st = h->st;
+  // host inputs: stage them in the handle's device buffers
+  const bool hostA = !is_device_ptr(A), hostB = !is_device_ptr(B), hostX = !is_device_ptr(X);
+  if (hostA != hostB || hostA != hostX) return -10;
+  double *dA = A, *dB = B, *dX = X;
+  int64_t dlda = lda, dldb = ldb, dldx = ldx;
+  GS_CUDA(cudaEventRecord(h->ev[0], st));
+  if (hostA) {
+    GS_TRY(h->hA.ensure((size_t)n * n * sizeof(double)));
+    GS_TRY(h->hB.ensure((size_t)n * n * sizeof(double)));
+    GS_TRY(h->hX.ensure((size_t)n * s * sizeof(double)));
+    dA = h->hA.d();
+    dB = h->hB.d();
+    dX = h->hX.d();
+    dlda = dldb = dldx = n;
+    GS_CUDA(cudaMemcpy2DAsync(dA, n * sizeof(double), A, lda * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpy2DAsync(dB, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyHostToDevice, st));
+  }
+  const int nb = nb_of(h, n);
+  FactorWork fw;
+  GS_TRY(factor_ws(h, n, nb, s, fw));
+  GS_TRY(h->hw.ensure((size_t)s * sizeof(double)));
+  // gs1: B = U^T U
+  GS_CUDA(cudaEventRecord(h->ev[1], st));
+  GS_TRY(potrf_blocked(st, n, dB, dldb, nb, fw));
+  int flag = 0;
+  GS_CUDA(cudaMemcpyAsync(&flag, fw.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaEventRecord(h->ev[2], st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    if (info) info->potrf_index = flag;
+    return GSYEIG_NOT_SPD;
+  }
+  // gs2: C = U^-T A U^-1 over A (diagonal-block inverses reused from gs1)
+  GS_TRY(sygst_blocked(st, n, dA, dlda, dB, dldb, nb, fw, true));
+  GS_CUDA(cudaEventRecord(h->ev[3], st));
+  // ke: Lanczos on C; Ritz vectors land in X
+  double ms_ke3 = 0;
+  int status = lanczos_run(h, dA, dlda, n, s, which, h->hw.d(), dX, dldx, info, &ms_ke3);
+  if (status != GSYEIG_SUCCESS && status != GSYEIG_NO_CONVERGENCE && status != GSYEIG_TIMEOUT) return status;
+  GS_CUDA(cudaEventRecord(h->ev[4], st));
+  // bt1: X = U^-1 Y
+  GS_TRY(trsm_back_blocked(st, n, dB, dldb, dX, dldx, s, nb, fw, true));
+  GS_CUDA(cudaMemcpyAsync(w, h->hw.p, (size_t)s * sizeof(double), cudaMemcpyDefault, st));
+  if (hostA)
+    GS_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), dX, n * sizeof(double), n * sizeof(double), s,
+                              cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaEventRecord(h->ev[8], st));
+  GS_TRY(finish(h));
+  prof.fill(info);
+  if (info) {
+    info->ms_gs1 = elapsed(h->ev[1], h->ev[2]);
+    info->ms_gs2 = elapsed(h->ev[2], h->ev[3]);
+    const double ke = elapsed(h->ev[3], h->ev[4]);
+    info->ms_ke3 = ms_ke3;
+    info->ms_ke = ke - ms_ke3;
+    info->ms_bt1 = elapsed(h->ev[4], h->ev[8]);
+    info->ms_total = elapsed(h->ev[0], h->ev[8]);
+    info->kernel_launches = g_launches.load() - l0;
+  }
+  return status;
+}
+
+}  // extern "C"

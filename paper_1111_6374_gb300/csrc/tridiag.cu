@@ -1,0 +1,357 @@
+// The small problems on the Lanczos tridiagonal T_m (m <= a few thousand):
+//   * eigenvalues by Sturm-count bisection (ke3; the paper's ARPACK uses a
+//     QR variant for this, Section 4.1 — bisection gives each Ritz value
+//     independently, one thread per value);
+//   * eigenvectors by inverse iteration (one thread per value, tridiagonal
+//     Gaussian elimination with partial pivoting), tight clusters
+//     orthogonalised afterwards;
+//   * the implicit restart (Section 2.3: "the application of the QR
+//     iteration to the tridiagonal matrix T_m"): p = m - k single-shift QR
+//     steps whose shifts are the unwanted Ritz values (exact shifts).  Each
+//     shift is a Givens bulge chase; after an exact shift the trailing
+//     entry deflates, so shift i chases over m - i rows.  The chase is
+//     sequential (one thread); the accumulation Q <- Q G^T, which is where
+//     the O(p m^2) flops are, runs on many CTAs, each owning rows of Q.
+#include <float.h>
+
+#include "lanczos.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int BIS_THREADS = 128;
+
+__device__ __forceinline__ double sturm_pivmin(double maxe2) { return DBL_MIN * fmax(1.0, maxe2); }
+
+// Number of eigenvalues of (d, e2 = e^2) strictly below x.
+__device__ int64_t sturm_below(int64_t m, const double *d, const double *e2, double x, double pivmin) {
+  int64_t cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0.0) cnt++;
+  for (int64_t i = 1; i < m; i++) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0.0) cnt++;
+  }
+  return cnt;
+}
+
+__device__ void block_minmax(double &lo, double &hi, double *sh) {
+  // sh: 2 * blockDim doubles
+  sh[threadIdx.x] = lo;
+  sh[blockDim.x + threadIdx.x] = hi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+      sh[blockDim.x + threadIdx.x] = fmax(sh[blockDim.x + threadIdx.x], sh[blockDim.x + threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  lo = sh[0];
+  hi = sh[blockDim.x];
+  __syncthreads();
+}
+
+// dynamic smem: d[m], e2[m], scratch[2*blockDim]
+__global__ void __launch_bounds__(BIS_THREADS) k_bisect(int64_t m, const double *__restrict__ d,
+                                                        const double *__restrict__ e, int64_t first, int64_t cnt,
+                                                        double *__restrict__ lam) {
+  extern __shared__ double sm[];
+  double *ds = sm, *e2 = sm + m, *sh = sm + 2 * m;
+  double lo = DBL_MAX, hi = -DBL_MAX, me2 = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    double di = d[i];
+    double el = (i > 0) ? fabs(e[i - 1]) : 0.0, er = (i + 1 < m) ? fabs(e[i]) : 0.0;
+    ds[i] = di;
+    e2[i] = (i + 1 < m) ? e[i] * e[i] : 0.0;
+    me2 = fmax(me2, er * er);
+    lo = fmin(lo, di - el - er);
+    hi = fmax(hi, di + el + er);
+  }
+  block_minmax(lo, hi, sh);
+  double tmp = -me2, dummy = 0.0;
+  block_minmax(tmp, dummy, sh);
+  me2 = -tmp;
+  const double pivmin = sturm_pivmin(me2);
+  const double span = fmax(fabs(lo), fabs(hi));
+  lo -= 2.0 * DBL_EPSILON * span + 2.0 * pivmin;
+  hi += 2.0 * DBL_EPSILON * span + 2.0 * pivmin;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const int64_t q = first + t;  // 0-based index of the wanted eigenvalue
+  double a = lo, b = hi;
+  for (int it = 0; it < 256; it++) {
+    double mid = 0.5 * (a + b);
+    if (b - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)) + 4.0 * pivmin || mid == a || mid == b) break;
+    if (sturm_below(m, ds, e2, mid, pivmin) > q)
+      b = mid;
+    else
+      a = mid;
+  }
+  lam[t] = 0.5 * (a + b);
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  return x ^ (x >> 33);
+}
+
+// Inverse iteration, one thread per eigenvalue.  Elimination of T - lam I
+// row by row with partial pivoting between the running row and the next
+// original row; U has two superdiagonals.  Work per thread: 5m doubles.
+__global__ void k_invit(int64_t m, const double *__restrict__ d, const double *__restrict__ e, int64_t cnt,
+                        const double *__restrict__ lam, double *__restrict__ Z, int64_t ldz, double *__restrict__ work) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  double *p0 = work + (size_t)t * 5 * m, *p1 = p0 + m, *p2 = p1 + m, *mu = p2 + m, *sw = mu + m;
+  double *z = Z + (size_t)t * ldz;
+  double tn = 0.0;
+  for (int64_t i = 0; i < m; i++) {
+    double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    tn = fmax(tn, r);
+  }
+  if (tn == 0.0) tn = 1.0;
+  const double tiny = DBL_EPSILON * tn;
+  const double x = lam[t];
+  // factor
+  double a = d[0] - x, b = (m > 1) ? e[0] : 0.0, c = 0.0;
+  for (int64_t i = 0; i < m; i++) {
+    if (i == m - 1) {
+      p0[i] = (fabs(a) < tiny) ? copysign(tiny, a) : a;
+      p1[i] = p2[i] = mu[i] = sw[i] = 0.0;
+      break;
+    }
+    const double lo = e[i], nd = d[i + 1] - x, nu = (i + 2 < m) ? e[i + 1] : 0.0;
+    if (fabs(a) >= fabs(lo)) {
+      const double piv = (fabs(a) < tiny) ? copysign(tiny, a) : a;
+      const double f = lo / piv;
+      p0[i] = piv; p1[i] = b; p2[i] = c; mu[i] = f; sw[i] = 0.0;
+      a = nd - f * b;
+      b = nu - f * c;
+    } else {
+      const double f = a / lo;
+      p0[i] = lo; p1[i] = nd; p2[i] = nu; mu[i] = f; sw[i] = 1.0;
+      a = b - f * nd;
+      b = c - f * nu;
+    }
+    c = 0.0;
+  }
+  // start vector
+  for (int64_t i = 0; i < m; i++) z[i] = 1.0 + 0.25 * ((double)(mix64((uint64_t)i * 0x9E3779B97F4A7C15ull + (uint64_t)t) >> 11) * 0x1p-53 - 0.5);
+  for (int it = 0; it < 3; it++) {
+    for (int64_t i = 0; i + 1 < m; i++) {
+      if (sw[i] != 0.0) { double q = z[i]; z[i] = z[i + 1]; z[i + 1] = q; }
+      z[i + 1] -= mu[i] * z[i];
+    }
+    double mx = 0.0;
+    for (int64_t i = m - 1; i >= 0; i--) {
+      double v = z[i];
+      if (i + 1 < m) v -= p1[i] * z[i + 1];
+      if (i + 2 < m) v -= p2[i] * z[i + 2];
+      v /= p0[i];
+      z[i] = v;
+      mx = fmax(mx, fabs(v));
+    }
+    const double s = (mx > 0.0) ? 1.0 / mx : 1.0;
+    for (int64_t i = 0; i < m; i++) z[i] *= s;
+  }
+  double nrm = 0.0;
+  for (int64_t i = 0; i < m; i++) nrm = fma(z[i], z[i], nrm);
+  nrm = sqrt(nrm);
+  const double s = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  for (int64_t i = 0; i < m; i++) z[i] *= s;
+}
+
+__device__ double block_sum256(double v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[i];
+  __syncthreads();
+  return s;  // valid in every thread
+}
+
+// Orthogonalise eigenvectors whose eigenvalues sit within 1e-10 ||T|| of
+// the previous one against the earlier members of their cluster (modified
+// Gram-Schmidt, two passes).  One CTA; a no-op scan when nothing clusters.
+__global__ void k_cluster_orth(int64_t m, int64_t cnt, const double *lam, double tn_hint, const double *d,
+                               const double *e, double *Z, int64_t ldz) {
+  __shared__ double red[32];
+  double tl = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x)
+    tl = fmax(tl, fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0));
+  // max-reduce
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tl = fmax(tl, __shfl_xor_sync(0xffffffffu, tl, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tl;
+  __syncthreads();
+  double tn = tn_hint;
+  for (int i = 0; i < (int)(blockDim.x >> 5); i++) tn = fmax(tn, red[i]);
+  __syncthreads();
+  const double thr = 1e-10 * tn;
+  int64_t start = 0;
+  for (int64_t c = 1; c < cnt; c++) {
+    if (lam[c] - lam[c - 1] > thr) {
+      start = c;
+      continue;
+    }
+    double *zc = Z + (size_t)c * ldz;
+    for (int pass = 0; pass < 2; pass++)
+      for (int64_t q = start; q < c; q++) {
+        const double *zq = Z + (size_t)q * ldz;
+        double acc = 0.0;
+        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) acc = fma(zq[i], zc[i], acc);
+        double dot = block_sum256(acc, red);
+        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) zc[i] -= dot * zq[i];
+        __syncthreads();
+      }
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) acc = fma(zc[i], zc[i], acc);
+    double nrm = sqrt(block_sum256(acc, red));
+    const double s = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) zc[i] *= s;
+    __syncthreads();
+  }
+}
+
+// Bulge chase for p exact shifts on T_m; rotations (c, s) of shift i at
+// rot[2 * (i * (m - 1) + r) + {0, 1}] for r < m - 1 - i.  One thread.
+__global__ void k_qr_chase(int64_t m, int64_t p, const double *alpha, const double *beta, const double *shifts,
+                           int dir, double *aP, double *bP, double *rot) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int64_t i = 0; i < m; i++) aP[i] = alpha[i];
+  for (int64_t i = 0; i + 1 < m; i++) bP[i] = beta[i];
+  for (int64_t sh = 0; sh < p; sh++) {
+    const int64_t hi = m - 1 - sh;  // active block [0, hi]
+    const double mu = (dir > 0) ? shifts[sh] : shifts[p - 1 - sh];
+    double *cs = rot + 2 * (size_t)sh * (m - 1);
+    double x = aP[0] - mu, z = (hi > 0) ? bP[0] : 0.0;
+    for (int64_t i = 0; i < hi; i++) {
+      double r = hypot(x, z);
+      double c = 1.0, s = 0.0;
+      if (r != 0.0) {
+        double ir = 1.0 / r;
+        c = x * ir;
+        s = z * ir;
+      }
+      if (i > 0) bP[i - 1] = r;
+      const double a0 = aP[i], a1 = aP[i + 1], b = bP[i];
+      const double cc = c * c, ss = s * s, c2s = 2.0 * c * s * b;
+      aP[i] = cc * a0 + c2s + ss * a1;
+      aP[i + 1] = ss * a0 - c2s + cc * a1;
+      bP[i] = c * s * (a1 - a0) + (cc - ss) * b;
+      if (i + 1 < hi) {
+        const double bulge = s * bP[i + 1];
+        bP[i + 1] *= c;
+        x = bP[i];
+        z = bulge;
+      }
+      cs[2 * i] = c;
+      cs[2 * i + 1] = s;
+    }
+  }
+}
+
+// Q = I, then Q <- Q G_1^T G_2^T ... for every rotation of every shift, one
+// thread per row of Q (rows are independent).
+__global__ void k_qr_apply(int64_t m, int64_t p, const double *__restrict__ rot, double *__restrict__ Q, int64_t ldq) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= m) return;
+  for (int64_t j = 0; j < m; j++) Q[r + (size_t)j * ldq] = (r == j) ? 1.0 : 0.0;
+  for (int64_t sh = 0; sh < p; sh++) {
+    const int64_t hi = m - 1 - sh;
+    const double *cs = rot + 2 * (size_t)sh * (m - 1);
+    double x = Q[r];
+    for (int64_t i = 0; i < hi; i++) {
+      const double c = cs[2 * i], s = cs[2 * i + 1];
+      const double y = Q[r + (size_t)(i + 1) * ldq];
+      Q[r + (size_t)i * ldq] = c * x + s * y;
+      x = c * y - s * x;
+    }
+    Q[r + (size_t)hi * ldq] = x;
+  }
+}
+
+__global__ void k_converged(int64_t m, int64_t cnt, const double *theta, const double *beta, const double *Z,
+                            int64_t ldz, double tol, LanczosState *state) {
+  __shared__ double red[32];
+  __shared__ int64_t nc;
+  if (threadIdx.x == 0) nc = 0;
+  __syncthreads();
+  const double tn = fmax(fabs(theta[0]), fabs(theta[m - 1]));
+  const double bm = fabs(beta[m - 1]);
+  double mx = 0.0;
+  int64_t mine = 0;
+  for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double est = bm * fabs(Z[(m - 1) + (size_t)i * ldz]);
+    double rel = (tn > 0.0) ? est / tn : est;
+    mx = fmax(mx, rel);
+    if (rel <= tol) mine++;
+  }
+  atomicAdd((unsigned long long *)&nc, (unsigned long long)mine);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) v = fmax(v, red[i]);
+    state->max_est = v;
+    state->nconv = nc;
+  }
+}
+
+}  // namespace
+
+int tri_bisect(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t first, int64_t cnt, double *lam) {
+  if (cnt <= 0) return GSYEIG_SUCCESS;
+  size_t smem = (size_t)(2 * m + 2 * BIS_THREADS) * sizeof(double);
+  if (smem > 48 * 1024)
+    GS_CUDA(cudaFuncSetAttribute((const void *)k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_bisect<<<(unsigned)ceil_div(cnt, BIS_THREADS), BIS_THREADS, smem, st>>>(m, d, e, first, cnt, lam);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int tri_invit(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t cnt, const double *lam, double *Z,
+              int64_t ldz, double *work) {
+  if (cnt <= 0) return GSYEIG_SUCCESS;
+  // one thread per eigenvalue, spread over many SMs (32 threads per CTA)
+  k_invit<<<(unsigned)ceil_div(cnt, 32), 32, 0, st>>>(m, d, e, cnt, lam, Z, ldz, work);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  k_cluster_orth<<<1, 256, 0, st>>>(m, cnt, lam, 0.0, d, e, Z, ldz);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int tri_qr_shifts(cudaStream_t st, int64_t m, int64_t p, const double *alpha, const double *beta, const double *shifts,
+                  int dir, double *alphaP, double *betaP, double *Q, int64_t ldq, double *rot) {
+  k_qr_chase<<<1, 32, 0, st>>>(m, p, alpha, beta, shifts, dir, alphaP, betaP, rot);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  k_qr_apply<<<(unsigned)ceil_div(m, 32), 32, 0, st>>>(m, p, rot, Q, ldq);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int tri_converged(cudaStream_t st, int64_t m, int64_t cnt, const double *theta_all, const double *beta, const double *Z,
+                  int64_t ldz, double tol, LanczosState *state) {
+  k_converged<<<1, 256, 0, st>>>(m, cnt, theta_all, beta, Z, ldz, tol, state);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+}  // namespace gs

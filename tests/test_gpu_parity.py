@@ -1,0 +1,228 @@
+"""GPU parity of every step of the KE route (Section 2.3) against the CPU
+FP64 oracle, called through the C ABI via the Python binding.
+
+Tolerances (all float64):
+  * potrf / sygst / trsm / symv: elementwise, 1e-11 relative to the
+    largest entry (the inputs have kappa(B) <= 5; different summation order
+    gives ~n eps).
+  * eigenvalues: |lam_gpu - lam_oracle| / |lam_oracle| <= 1e-10.
+  * per-column backward error eta <= 1e-10, ||X^T B X - I||_max <= 1e-10.
+  * eigenvectors: largest principal angle of each cluster (B inner
+    product) within the Davis-Kahan bound for the 1e-12 ||C|| Ritz
+    tolerance (see _checks.max_subspace_angle).
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+import oracle
+from tests import _checks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_6374_gb300 import Solver
+
+    return Solver(0)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _cm(a: np.ndarray) -> torch.Tensor:
+    """numpy matrix -> column-major CUDA tensor"""
+    t = torch.empty((a.shape[1], a.shape[0]), dtype=torch.float64, device="cuda").t()
+    t.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+    return t
+
+
+@pytest.mark.parametrize("n", [1, 37, 64, 200, 513, 1000])
+def test_potrf_matches_oracle(solver, n):
+    A, B, _ = inputs.make_pencil(max(n, 2), seed=n)
+    B = B[:n, :n].numpy()
+    dB = _cm(B)
+    assert solver.potrf(dB) == 0
+    U = np.triu(_np(dB))
+    Uo = oracle.potrf(B)
+    assert np.abs(U - Uo).max() <= 1e-11 * np.abs(Uo).max()
+    # strictly lower triangle untouched
+    assert np.array_equal(np.tril(_np(dB), -1), np.tril(B, -1))
+
+
+def test_potrf_reports_first_bad_pivot(solver):
+    B = inputs.make_pencil(300, seed=5)[1].numpy().copy()
+    B[150, 150] = -1.0
+    with pytest.raises(oracle.NotSPD) as ei:
+        oracle.potrf(B)
+    assert solver.potrf(_cm(B)) == ei.value.index == 151
+
+
+@pytest.mark.parametrize("n", [2, 65, 300, 777])
+def test_sygst_matches_oracle(solver, n):
+    A, B, _ = (t.numpy() for t in inputs.make_pencil(n, seed=10 + n))
+    U = oracle.potrf(B)
+    Co = oracle.sygst(A, U)
+    Ain = A.copy()
+    Ain[np.triu_indices(n, 1)] = 0.0  # only the lower triangle may be read
+    dA = _cm(Ain)
+    solver.sygst(dA, _cm(U))
+    C = _np(dA)
+    assert np.abs(C - Co).max() <= 1e-11 * np.abs(Co).max()
+    assert np.array_equal(C, C.T)
+
+
+@pytest.mark.parametrize("n", [1, 31, 64, 1001, 4096])
+def test_symv_matches_oracle(solver, n):
+    r = np.random.default_rng(n)
+    M = r.standard_normal((n, n))
+    C = M + M.T
+    w = r.standard_normal(n)
+    z = _np(solver.symv(_cm(C), torch.from_numpy(w).cuda()))
+    ref = (C.astype(np.longdouble) @ w.astype(np.longdouble)).astype(np.float64)
+    # deterministic worst-case-style bound 2 n eps max|C| max|w| (real errors are far smaller)
+    assert np.abs(z - ref).max() <= 2 * n * np.finfo(float).eps * np.abs(C).max() * np.abs(w).max()
+
+
+@pytest.mark.parametrize("n,s", [(1, 1), (100, 1), (257, 7), (1000, 64)])
+def test_trsm_back_matches_oracle(solver, n, s):
+    B = inputs.make_pencil(max(n, 2), seed=3 * n)[1][:n, :n].numpy()
+    U = oracle.potrf(B)
+    Y = np.random.default_rng(s).standard_normal((n, s))
+    Xo = oracle.backsolve(U, Y)
+    dY = _cm(Y)
+    solver.trsm_back(_cm(U), dY)
+    X = _np(dY)
+    assert np.abs(X - Xo).max() <= 1e-11 * np.abs(Xo).max()
+
+
+@pytest.mark.parametrize("m,clustered", [(1, False), (2, False), (30, False), (300, False), (300, True), (777, False)])
+def test_tridiag_eig_matches_oracle(solver, m, clustered):
+    d, e = inputs.make_tridiagonal(m, seed=m, clustered=clustered)
+    w_or = oracle.tql(d.numpy(), e.numpy())
+    first, cnt = (0, m) if m <= 30 else (m // 3, m // 3)
+    lam, Z = solver.tridiag_eig(d.cuda(), e.cuda(), first, cnt)
+    lam, Z = _np(lam), _np(Z)
+    tn = np.abs(w_or).max()
+    assert np.abs(lam - w_or[first:first + cnt]).max() <= 1e-12 * tn
+    T = np.diag(d.numpy()) + np.diag(e.numpy(), 1) + np.diag(e.numpy(), -1)
+    assert np.abs(T @ Z - Z * lam).max() <= 1e-10 * tn
+    assert np.abs(Z.T @ Z - np.eye(cnt)).max() <= 1e-10
+
+
+def _check_pairs(A, B, w, X, w_ref, lam_all, label=""):
+    s = len(w)
+    rel = np.abs(w - w_ref) / np.abs(w_ref)
+    assert rel.max() <= 1e-10, (label, rel.max())
+    et = _checks.eta(A, B, w, X)
+    assert et.max() <= 1e-10, (label, et.max())
+    assert _checks.b_orth_err(B, X) <= 1e-10, label
+    return et
+
+
+@pytest.mark.parametrize("n,s,which", [(512, 10, "smallest"), (512, 10, "largest"), (257, 5, "smallest"),
+                                       (1000, 37, "smallest"), (20, 19, "smallest"), (3, 1, "largest")])
+def test_solve_matches_oracle(solver, n, s, which):
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=n + s))
+    w_or, X_or = oracle.gsyeig(A, B, s, which=which)
+    w, X, info = solver.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s, which=which)
+    w, X = _np(w), _np(X)
+    assert info["nconv"] >= s
+    _check_pairs(A, B, w, X, w_or, lam, f"n={n} s={s}")
+    ref_lam = lam[:s] if which == "smallest" else lam[-s:]
+    assert np.max(np.abs(w - ref_lam) / np.abs(ref_lam)) <= 1e-10
+    cn = np.abs(lam).max()
+    ang, lim = _checks.max_subspace_angle(B, X, X_or, w, lam, cn, 1e-12 * cn)
+    assert ang <= lim, (ang, lim)
+
+
+def test_solve_host_pointers_match_device(solver):
+    A, B, lam = inputs.make_pencil(300, seed=77)
+    w_d, X_d, _ = solver.solve(A.cuda(), B.cuda(), 8)
+    w_h, X_h, info = solver.solve(A.clone(), B.clone(), 8)
+    assert not w_h.is_cuda and not X_h.is_cuda
+    assert torch.equal(w_h, w_d.cpu())
+    assert torch.equal(X_h, X_d.cpu())
+
+
+def test_syev_lanczos_matches_oracle_on_c(solver):
+    n, s = 600, 12
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=4))
+    C = oracle.sygst(A, oracle.potrf(B))
+    d, e, _, _ = oracle.tridiag(C)
+    w_all = oracle.tql(d, e)
+    w, Y, info = solver.syev_lanczos(torch.from_numpy(C).cuda(), s)
+    w, Y = _np(w), _np(Y)
+    assert np.max(np.abs(w - w_all[:s]) / np.abs(w_all[:s])) <= 1e-10
+    assert np.abs(Y.T @ Y - np.eye(s)).max() <= 1e-12
+    assert np.abs(C @ Y - Y * w).max() <= 1e-9
+
+
+def test_invalid_arguments(solver):
+    from paper_1111_6374_gb300 import GsyeigError
+
+    A, B, _ = inputs.make_pencil(16, seed=1)
+    with pytest.raises(GsyeigError) as ei:
+        solver.solve(A.cuda(), B.cuda(), 16)
+    assert ei.value.status == -7
+    with pytest.raises(GsyeigError) as ei:
+        solver.solve(A.cuda(), B.cuda(), 0)
+    assert ei.value.status == -7
+
+
+def test_not_spd_through_solve(solver):
+    from paper_1111_6374_gb300 import GsyeigError
+
+    A, B, _ = inputs.make_pencil(200, seed=9)
+    B[100, 100] = -5.0
+    with pytest.raises(GsyeigError) as ei:
+        solver.solve(A.cuda(), B.cuda(), 4)
+    assert ei.value.status == 1
+
+
+def test_no_convergence_and_timeout_statuses():
+    from paper_1111_6374_gb300 import Solver
+
+    A, B, lam = inputs.make_pencil(2000, seed=2)
+    s1 = Solver(0, max_restarts=0)
+    w, X, info = s1.solve(A.cuda(), B.cuda(), 20, allow_unconverged=True)
+    assert info["status"] == 2 and info["nconv"] < 20 and info["restarts"] == 0
+    s2 = Solver(0, timeout_ms=1e-3)
+    w, X, info = s2.solve(A.cuda(), B.cuda(), 20, allow_unconverged=True)
+    assert info["status"] == 3
+
+
+def test_full_size_workload_properties(solver):
+    """n = 16384, s = 100 smallest (the benchmark workload): every pair is
+    checked against the constructed spectrum, the backward error and
+    B-orthonormality (the oracle cannot run at this size in test time)."""
+    n, s = 16384, 100
+    A, B, lam = inputs.make_pencil(n, seed=0, device="cuda")
+    w, X, info = solver.solve(A, B, s)
+    assert info["nconv"] >= s
+    lam_s = lam[:s]
+    assert float(((w - lam_s).abs() / lam_s.abs()).max()) <= 1e-10
+    # backward errors on the GPU in float64 (torch matmul used as a checker)
+    nA = float(torch.linalg.matrix_norm(A, ord=2)) if n <= 4096 else _power(A)
+    nB = _power(B)
+    R = A @ X - (B @ X) * w
+    et = R.norm(dim=0) / ((nA + w.abs() * nB) * X.norm(dim=0))
+    assert float(et.max()) <= 1e-10
+    G = X.T @ (B @ X)
+    assert float((G - torch.eye(s, device=G.device, dtype=G.dtype)).abs().max()) <= 1e-10
+
+
+def _power(M, iters=30):
+    v = torch.randn(M.shape[0], device=M.device, dtype=M.dtype, generator=torch.Generator(device=M.device).manual_seed(0))
+    v /= v.norm()
+    lamb = 0.0
+    for _ in range(iters):
+        w = M @ v
+        lamb = float(w.norm())
+        v = w / lamb
+    return lamb

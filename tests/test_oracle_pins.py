@@ -230,3 +230,22 @@ def test_block_diagonal_pencil():
     w, X = oracle.gsyeig(A, B, 4)
     assert np.abs(w - np.array([1.0, 1.0, 3.0, 5.0])).max() < 1e-14
     assert np.abs(X.T @ B @ X - np.eye(4)).max() < 1e-14
+
+
+def test_subspace_angle_helper_detects_rotation():
+    """The parity tests' eigenvector metric: zero for identical bases, the
+    rotation angle for a basis rotated by a known angle."""
+    from tests import _checks
+
+    n = 40
+    B = np.eye(n)
+    X = np.eye(n)[:, :3]
+    w = np.array([1.0, 2.0, 3.0])
+    lam = np.arange(1.0, n + 1)
+    ang, _ = _checks.max_subspace_angle(B, X, X, w, lam, 40.0, 1e-12)
+    assert ang < 1e-15
+    t = 1e-6
+    Y = X.copy()
+    Y[:, 1] = np.cos(t) * X[:, 1] + np.sin(t) * np.eye(n)[:, 10]
+    ang, _ = _checks.max_subspace_angle(B, Y, X, w, lam, 40.0, 1e-12)
+    assert abs(ang - np.sin(t)) < 1e-12
