@@ -50,7 +50,8 @@ enum {
   GSYEIG_TIMEOUT = 3,        /* the wall-clock budget opts.timeout_ms ran out between restarts */
   GSYEIG_CUDA_ERROR = 4,     /* a CUDA runtime call failed; the handle should be destroyed */
   GSYEIG_OOM = 5,            /* device workspace could not be allocated */
-  GSYEIG_NOT_SUPPORTED = 6   /* option combination not available */
+  GSYEIG_NOT_SUPPORTED = 6,  /* option combination not available */
+  GSYEIG_SCRATCH_TOO_SMALL = 7 /* gsyeig_tridiag_eig_noalloc: 5*m*cnt exceeds its fixed scratch */
 };
 
 /* Solver options (gsyeig_default_options fills the defaults). */
@@ -151,6 +152,25 @@ int gsyeig_syev_lanczos(gsyeig_handle h, const double *dC, int64_t ldc, int64_t 
  * by inverse iteration (m x cnt, ldz).  All pointers device. */
 int gsyeig_tridiag_eig(gsyeig_handle h, const double *d, const double *e, int64_t m, int64_t first, int64_t cnt,
                        double *lam, double *dZ, int64_t ldz);
+
+/* Allocation-free form of gsyeig_tridiag_eig (same results).  The paper has
+ * no counterpart; it is here for callers that cannot allocate device memory
+ * when they need this solve: code whose device memory belongs entirely to
+ * another allocator or a fixed budget, and latency-critical loops in which a
+ * cudaMalloc/cudaFree would synchronise the device.  No handle and no
+ * allocation: the inverse-iteration scratch is a fixed 8 MiB array inside
+ * the library (held on every GPU that loads it until the process exits), so
+ * with dZ != NULL the call requires 5 * m * cnt <= 1048576 and otherwise
+ * returns GSYEIG_SCRATCH_TOO_SMALL without touching the outputs.  Runs on
+ * the calling thread's current device, on `cuda_stream` (cudaStream_t, NULL =
+ * legacy default stream), synchronous on return.  The first call on a device
+ * looks up the scratch address for that device; make that first call before
+ * any stream capture.  All calls share the one scratch array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  Argument codes: -1 d, -2 e, -3 m, -4 first,
+ * -5 cnt, -6 lam, -8 ldz. */
+int gsyeig_tridiag_eig_noalloc(const double *d, const double *e, int64_t m, int64_t first, int64_t cnt, double *lam,
+                               double *dZ, int64_t ldz, void *cuda_stream);
 
 /* Number of kernels this library has launched in the calling process. */
 int64_t gsyeig_kernel_launches(void);

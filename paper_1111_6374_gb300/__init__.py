@@ -20,10 +20,12 @@ import torch
 
 from .build import LIB, build as _build_lib
 
-__all__ = ["Solver", "load", "colmajor", "colmajor_empty", "Info", "GsyeigError", "kernel_launches"]
+__all__ = ["Solver", "load", "colmajor", "colmajor_empty", "Info", "GsyeigError", "kernel_launches",
+           "tridiag_eig_noalloc"]
 
 SMALLEST, LARGEST = 0, 1
-_STATUS = {1: "NOT_SPD", 2: "NO_CONVERGENCE", 3: "TIMEOUT", 4: "CUDA_ERROR", 5: "OOM", 6: "NOT_SUPPORTED"}
+_STATUS = {1: "NOT_SPD", 2: "NO_CONVERGENCE", 3: "TIMEOUT", 4: "CUDA_ERROR", 5: "OOM", 6: "NOT_SUPPORTED",
+           7: "SCRATCH_TOO_SMALL"}
 
 
 class GsyeigError(RuntimeError):
@@ -80,6 +82,7 @@ def load(build_if_missing: bool = True):
         "gsyeig_syev_lanczos": ([vp, vp, i64, i64, i64, i32, vp, vp, i64, ctypes.POINTER(Info)], i32),
         "gsyeig_tridiag_eig": ([vp, vp, vp, i64, i64, i64, vp, vp, i64], i32),
         "gsyeig_kernel_launches": ([], i64),
+        "gsyeig_tridiag_eig_noalloc": ([vp, vp, i64, i64, i64, vp, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -91,6 +94,25 @@ def load(build_if_missing: bool = True):
 
 def kernel_launches() -> int:
     return int(load().gsyeig_kernel_launches())
+
+
+def tridiag_eig_noalloc(d: torch.Tensor, e: torch.Tensor, first: int, cnt: int, vectors: bool = True,
+                        stream: torch.cuda.Stream | None = None):
+    """Allocation-free tridiagonal eigen-solve (gsyeig_tridiag_eig_noalloc):
+    the library allocates nothing; the caller provides the outputs, which this
+    wrapper allocates with torch.  Returns (lam, Z) or lam."""
+    _check_f64(d, e)
+    lib = load()
+    m = d.shape[0]
+    lam = torch.empty(cnt, device=d.device, dtype=torch.float64)
+    Z = colmajor_empty(m, cnt, device=d.device) if vectors else None
+    s = stream if stream is not None else torch.cuda.current_stream(d.device)
+    st = lib.gsyeig_tridiag_eig_noalloc(d.data_ptr(), e.data_ptr() if e.numel() else None, m, first, cnt,
+                                        lam.data_ptr(), Z.data_ptr() if vectors else None, m,
+                                        ctypes.c_void_p(s.cuda_stream))
+    if st != 0:
+        raise GsyeigError(st, "tridiag_eig_noalloc: " + lib.gsyeig_strerror(st).decode())
+    return (lam, Z) if vectors else lam
 
 
 def colmajor_empty(rows: int, cols: int, device="cuda", dtype=torch.float64) -> torch.Tensor:

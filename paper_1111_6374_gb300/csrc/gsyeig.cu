@@ -381,6 +381,8 @@ const char *gsyeig_strerror(int status) {
     case GSYEIG_CUDA_ERROR: return "CUDA runtime error";
     case GSYEIG_OOM: return "out of device memory";
     case GSYEIG_NOT_SUPPORTED: return "unsupported parameter combination";
+    case GSYEIG_SCRATCH_TOO_SMALL:
+      return "problem too large for the fixed scratch of the allocation-free entry point (needs 5*m*cnt <= 1048576 doubles)";
     default: return status < 0 ? "invalid argument" : "unknown status";
   }
 }

@@ -14,6 +14,8 @@
 //     the O(p m^2) flops are, runs on many CTAs, each owning rows of Q.
 #include <float.h>
 
+#include <mutex>
+
 #include "lanczos.cuh"
 
 namespace gs {
@@ -355,3 +357,75 @@ int tri_converged(cudaStream_t st, int64_t m, int64_t cnt, const double *theta_a
 }
 
 }  // namespace gs
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the tridiagonal eigen-solve (the paper has no
+// counterpart: this exists for callers, not for the method).
+//
+// gsyeig_tridiag_eig draws its inverse-iteration scratch (5 m cnt doubles)
+// from a handle workspace that grows with cudaMalloc.  Some callers cannot
+// allocate device memory at the point where they need this solve: code whose
+// device memory is entirely owned by another allocator or a fixed budget,
+// and latency-critical loops where cudaMalloc/cudaFree would synchronise the
+// whole device.  This entry point takes only the caller's inputs and
+// outputs; its scratch is the fixed array below, which lives in the
+// library's own module image, so every GPU that loads the library holds
+// these 8 MiB until the process exits.
+//
+// Host code may not use g_noalloc_scratch directly: on the host that name
+// is a stand-in symbol, not a device address.  The device address is looked
+// up once per device with cudaGetSymbolAddress, with that device current,
+// on the first call made on that device.
+// ---------------------------------------------------------------------------
+namespace gs {
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;  // 8 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (set-up on
+// first use per device).
+int noalloc_scratch(double **out) {
+  int dev = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return GSYEIG_NOT_SUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    GS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return GSYEIG_SUCCESS;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" int gsyeig_tridiag_eig_noalloc(const double *d, const double *e, int64_t m, int64_t first, int64_t cnt,
+                                          double *lam, double *dZ, int64_t ldz, void *cuda_stream) {
+  using namespace gs;
+  if (!d) return -1;
+  if (!e && m > 1) return -2;
+  if (m < 1) return -3;
+  if (first < 0 || first >= m) return -4;
+  if (cnt < 1 || first + cnt > m) return -5;
+  if (!lam) return -6;
+  if (dZ && ldz < m) return -8;
+  if (dZ && (size_t)5 * (size_t)m * (size_t)cnt > kNoAllocScratchDoubles) return GSYEIG_SCRATCH_TOO_SMALL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  double *scratch = nullptr;
+  if (dZ) GS_TRY(noalloc_scratch(&scratch));
+  GS_TRY(tri_bisect(st, m, d, e, first, cnt, lam));
+  // inverse iteration writes every scratch entry before reading it, so the
+  // previous call's contents need no clearing
+  if (dZ) GS_TRY(tri_invit(st, m, d, e, cnt, lam, dZ, ldz, scratch));
+  GS_CUDA(cudaStreamSynchronize(st));
+  GS_CUDA(cudaGetLastError());
+  return GSYEIG_SUCCESS;
+}
