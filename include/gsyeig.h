@@ -47,7 +47,8 @@ enum {
   GSYEIG_SUCCESS = 0,
   GSYEIG_NOT_SPD = 1,        /* Cholesky of B met a non-positive pivot (Eq. 2); see info.potrf_index */
   GSYEIG_NO_CONVERGENCE = 2, /* max_restarts reached with fewer than s converged pairs; best pairs returned */
-  GSYEIG_TIMEOUT = 3,        /* the wall-clock budget opts.timeout_ms ran out between restarts */
+  GSYEIG_TIMEOUT = 3,        /* opts.timeout_ms ran out between restarts, or a bounded device-side wait
+                                of the tensor-core GEMM expired (results then invalid) */
   GSYEIG_CUDA_ERROR = 4,     /* a CUDA runtime call failed; the handle should be destroyed */
   GSYEIG_OOM = 5,            /* device workspace could not be allocated */
   GSYEIG_NOT_SUPPORTED = 6,  /* option combination not available */
@@ -56,16 +57,27 @@ enum {
 
 /* Solver options (gsyeig_default_options fills the defaults). */
 typedef struct {
-  double tol;           /* accept Ritz pair i when |beta_m s_{m,i}| <= tol * max|theta| (default 1e-12) */
+  double tol;           /* accept Ritz pair i when |beta_m s_{m,i}| <= tol * ||T|| (running estimate; default 1e-12) */
   int64_t krylov_dim;   /* m, Lanczos basis size, s < m <= n; 0 = min(n, max(3s, s + 16)) */
   int64_t keep;         /* k, vectors kept at a restart, s <= k < m; 0 = min(s + max(2, s/4), m - 1) */
   int64_t max_restarts; /* default 2000 */
   uint64_t seed;        /* seed of the counter-based start vector (default 0) */
   const double *v0;     /* optional device start vector of length n (NULL = random) */
   double timeout_ms;    /* 0 = none; checked between restarts only */
-  int32_t block;        /* panel width nb of the blocked factorisations, 16..160; 0 = default (64) */
+  int32_t block;        /* panel width nb of the blocked factorisations, 16..160; 0 = default (128) */
   int32_t profile;      /* 1 = time every GEMM-engine and symv launch with CUDA events on the
                            library stream and report them in gsyeig_info (small overhead) */
+  int32_t fp64_gemm;    /* 0 (default): the O(n^3) GEMMs of gs1/gs2/bt1 with K <= 128 run on the bf16
+                           tensor cores (tcgen05) by error-free slicing (FP64-accurate, normwise);
+                           1: plain FP64 FMA; 2: the same slicing on the legacy mma.sync path */
+  int32_t fp64_symv;    /* 0 (default): ke1 streams C's lower triangle as fp32 hi/lo tiles built once per
+                           solve (C_hi + C_lo = C to ~2^-48) with compensated fp32 products, HBM-bound;
+                           1: plain FP64 product over the full square of C */
+  int32_t qr_restart;   /* 0 (default): thick restart -- keep the k wanted Ritz vectors and continue from
+                           the last Lanczos vector (the same subspace and projection as an exact-shift
+                           implicit restart, computed in parallel); 1: implicit restart by p = m - k
+                           exact-shift QR steps on T_m (Givens bulge chase), as ARPACK does */
+  int32_t reserved;     /* must be 0 */
 } gsyeig_opts;
 
 /* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
@@ -86,6 +98,9 @@ typedef struct {
   int64_t gemm_launches, symv_launches;
   double gemm_ms, gemm_flops, gemm_bytes;
   double symv_ms, symv_flops, symv_bytes;
+  /* opts.profile = 1: event time of the Lanczos bookkeeping (ke2): reorthogonalisation and
+   * normalisation, restarts (QR iteration on T_m and V_m Q), Ritz problems on T_m */
+  double orth_ms, restart_ms, ritz_ms;
 } gsyeig_info;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t

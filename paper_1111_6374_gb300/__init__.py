@@ -37,7 +37,9 @@ class GsyeigError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("krylov_dim", ctypes.c_int64), ("keep", ctypes.c_int64),
                 ("max_restarts", ctypes.c_int64), ("seed", ctypes.c_uint64), ("v0", ctypes.c_void_p),
-                ("timeout_ms", ctypes.c_double), ("block", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("timeout_ms", ctypes.c_double), ("block", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("fp64_gemm", ctypes.c_int32), ("fp64_symv", ctypes.c_int32),
+                ("qr_restart", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -47,7 +49,7 @@ class Info(ctypes.Structure):
                                                 "max_ritz_estimate")] + \
                [(f, ctypes.c_int64) for f in ("gemm_launches", "symv_launches")] + \
                [(f, ctypes.c_double) for f in ("gemm_ms", "gemm_flops", "gemm_bytes", "symv_ms", "symv_flops",
-                                                "symv_bytes")]
+                                                "symv_bytes", "orth_ms", "restart_ms", "ritz_ms")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

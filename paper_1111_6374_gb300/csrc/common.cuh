@@ -62,7 +62,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // call has synchronised.  One profiler per handle, installed for the
 // duration of an API call on the calling thread.
 // ---------------------------------------------------------------------------
-enum ProfClass { PROF_GEMM = 0, PROF_SYMV = 1, PROF_NCLASS = 2 };
+enum ProfClass { PROF_GEMM = 0, PROF_SYMV = 1, PROF_ORTH = 2, PROF_RESTART = 3, PROF_RITZ = 4, PROF_NCLASS = 5 };
 
 struct KernelProfiler {
   std::vector<cudaEvent_t> pool;
@@ -98,6 +98,28 @@ enum TriMode { TRI_ALL = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
 int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
           const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
           TriMode mode = TRI_ALL, int64_t diag = 0, const int *abort_flag = nullptr);
+
+// How dgemm executes, installed per API call: sliced = true routes every
+// call with 1 <= K <= 128 to the error-free bf16 tensor-core GEMM
+// (gemm_sliced.cu) using the workspace ws; otherwise the FP64 FMA kernel.
+struct GemmContext {
+  bool sliced = false;
+  bool umma = true;     // tcgen05 engine (else mma.sync engine)
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  int *err = nullptr;   // device flag: a bounded wait inside the tcgen05 engine expired
+};
+GemmContext *&current_gemm();
+
+size_t umma_workspace_bytes(int64_t M, int64_t N, int64_t K);
+int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
+              const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+              TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err);
+
+size_t sliced_workspace_bytes(int64_t M, int64_t N, int64_t K);
+int sliced_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
+                const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes);
 
 // Copy an M x N block (column-major, both with leading dimensions).
 int copy_block(cudaStream_t st, int64_t M, int64_t N, const double *src, int64_t lds, double *dst, int64_t ldd,

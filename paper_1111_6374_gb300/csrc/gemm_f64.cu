@@ -25,6 +25,11 @@ KernelProfiler *&current_profiler() {
   return p;
 }
 
+GemmContext *&current_gemm() {
+  static thread_local GemmContext *g = nullptr;
+  return g;
+}
+
 size_t KernelProfiler::start(cudaStream_t st) {
   if (used + 2 > pool.size()) {
     size_t grow = std::max<size_t>(256, pool.size());
@@ -211,13 +216,22 @@ int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64
           int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, TriMode mode, int64_t diag,
           const int *abort_flag) {
   if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
-  dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
   KernelProfiler *prof = current_profiler();
   size_t e0 = prof ? prof->start(st) : SIZE_MAX;
-  k_dgemm<<<grid, NT, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, (int)mode, diag,
-                               abort_flag);
-  count_launch();
-  GS_CHECK_LAUNCH();
+  GemmContext *gc = current_gemm();
+  if (gc && gc->sliced && gc->umma && K >= 1 && K <= 128 && gc->ws_bytes >= umma_workspace_bytes(M, N, K)) {
+    GS_TRY(umma_gemm(st, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, mode, diag, abort_flag,
+                     gc->ws, gc->ws_bytes, gc->err));
+  } else if (gc && gc->sliced && !gc->umma && K >= 1 && K <= 128 && gc->ws_bytes >= sliced_workspace_bytes(M, N, K)) {
+    GS_TRY(sliced_gemm(st, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, mode, diag, abort_flag,
+                       gc->ws, gc->ws_bytes));
+  } else {
+    dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
+    k_dgemm<<<grid, NT, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, (int)mode, diag,
+                                 abort_flag);
+    count_launch();
+    GS_CHECK_LAUNCH();
+  }
   if (prof) {
     const double el = region_elems(M, N, mode, diag);
     // algorithmic: 2K flops per written element; bytes: op(A), op(B) once, C read (beta != 0) and written

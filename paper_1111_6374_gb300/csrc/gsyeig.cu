@@ -9,6 +9,7 @@
 #include <new>
 
 #include "lanczos.cuh"
+#include "symv_df.cuh"
 
 namespace gs {
 
@@ -49,14 +50,20 @@ struct gsyeig_ctx {
   gsyeig_opts opts{};
   // workspace
   DevBuf uinv, panel, flag;
-  DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts;
+  DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts, arrow;
   DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
+  DevBuf gemm_ws;         // slices of the tensor-core GEMM
+  DevBuf gemm_err;        // device error flag of the tcgen05 engine
+  DevBuf dfop, dfpart;    // double-float operator tiles and symv partials
+  DfOperator op;
+  bool use_df = false;
   KernelProfiler prof;
+  GemmContext gemm;
 };
 
 namespace {
 
-constexpr int kDefaultBlock = 64;
+constexpr int kDefaultBlock = 128;
 
 // Installs the handle's profiler for the duration of one API call when
 // opts.profile is set; fills the profile fields of info on request.
@@ -80,6 +87,9 @@ struct ProfScope {
     info->symv_ms = ms[PROF_SYMV];
     info->symv_flops = fl[PROF_SYMV];
     info->symv_bytes = by[PROF_SYMV];
+    info->orth_ms = ms[PROF_ORTH];
+    info->restart_ms = ms[PROF_RESTART];
+    info->ritz_ms = ms[PROF_RITZ];
   }
   ~ProfScope() {
     if (on) {
@@ -118,7 +128,43 @@ int nb_of(gsyeig_handle h, int64_t n) {
   return nb;
 }
 
+// Install the GEMM mode for this call; the sliced GEMM needs slices of two
+// operands of at most max(n, s) rows and nb columns.
+int gemm_setup(gsyeig_handle h, int64_t n, int nb, int64_t s) {
+  h->gemm.sliced = (h->opts.fp64_gemm != 1) && nb <= 128;
+  h->gemm.umma = (h->opts.fp64_gemm == 0);
+  if (h->gemm.sliced) {
+    const int64_t r = std::max<int64_t>(n, s);
+    GS_TRY(h->gemm_ws.ensure(std::max(sliced_workspace_bytes(r, r, nb), umma_workspace_bytes(r, r, nb))));
+    h->gemm.ws = h->gemm_ws.p;
+    h->gemm.ws_bytes = h->gemm_ws.bytes;
+    GS_TRY(h->gemm_err.ensure(64));
+    h->gemm.err = static_cast<int *>(h->gemm_err.p);
+    GS_CUDA(cudaMemsetAsync(h->gemm.err, 0, sizeof(int), h->st));  // cudaMalloc does not zero
+  }
+  current_gemm() = &h->gemm;
+  return GSYEIG_SUCCESS;
+}
+
+// After a call that used the tcgen05 engine: did any of its bounded waits expire?
+int gemm_check(gsyeig_handle h) {
+  if (!h->gemm.sliced || !h->gemm.umma || !h->gemm.err) return GSYEIG_SUCCESS;
+  int e = 0;
+  GS_CUDA(cudaMemcpyAsync(&e, h->gemm.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  GS_CUDA(cudaStreamSynchronize(h->st));
+  if (e) {
+    GS_CUDA(cudaMemsetAsync(h->gemm.err, 0, sizeof(int), h->st));
+    return GSYEIG_TIMEOUT;
+  }
+  return GSYEIG_SUCCESS;
+}
+
+struct GemmScope {
+  ~GemmScope() { current_gemm() = nullptr; }
+};
+
 int factor_ws(gsyeig_handle h, int64_t n, int nb, int64_t s, FactorWork &w) {
+  GS_TRY(gemm_setup(h, n, nb, s));
   const int64_t nblk = ceil_div(n, nb);
   GS_TRY(h->uinv.ensure((size_t)nblk * nb * nb * sizeof(double)));
   GS_TRY(h->panel.ensure((size_t)std::max<int64_t>(n, s) * nb * sizeof(double) + 64));
@@ -149,10 +195,27 @@ LanczosParams lanczos_params(const gsyeig_opts &o, int64_t n, int64_t s) {
   return {m, k};
 }
 
+// Coarse profiled region on the library stream (no-op without a profiler).
+struct ProfRegion {
+  cudaStream_t st;
+  int cls;
+  size_t e0 = SIZE_MAX;
+  ProfRegion(cudaStream_t s, int c) : st(s), cls(c) {
+    if (current_profiler()) e0 = current_profiler()->start(st);
+  }
+  ~ProfRegion() {
+    if (current_profiler()) current_profiler()->stop(st, e0, cls, 0.0, 0.0);
+  }
+};
+
 // One Lanczos step j: z = C v_j, CGS2 against v_0..v_j, alpha_j, beta_j, v_{j+1}.
 int lanczos_step(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t m, int64_t j, const double *C, int64_t ldc) {
   double *V = h->V.d(), *z = h->z.d();
-  GS_TRY(symv_f64(st, n, C, ldc, V + (size_t)j * n, z));
+  if (h->use_df)
+    GS_TRY(df_symv(st, h->op, V + (size_t)j * n, z));
+  else
+    GS_TRY(symv_f64(st, n, C, ldc, V + (size_t)j * n, z));
+  ProfRegion pr(st, PROF_ORTH);
   GS_TRY(lz_cgs2(st, n, j + 1, V, n, z, h->h1.d(), h->h2.d(), h->sq.d()));
   GS_TRY(lz_finalize(st, j, m, h->h1.d(), h->h2.d(), h->sq.d(), lz_nparts(n), h->alpha.d(), h->beta.d(),
                      static_cast<LanczosState *>(h->state.p)));
@@ -192,12 +255,24 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
   GS_TRY(h->alphaP.ensure((size_t)m * sizeof(double)));
   GS_TRY(h->betaP.ensure((size_t)m * sizeof(double)));
   GS_TRY(h->theta.ensure((size_t)m * sizeof(double)));
-  GS_TRY(h->S.ensure((size_t)m * s * sizeof(double)));
+  GS_TRY(h->S.ensure((size_t)m * k * sizeof(double)));
+  GS_TRY(h->arrow.ensure((size_t)m * sizeof(double)));
   GS_TRY(h->Q.ensure((size_t)m * m * sizeof(double)));
   GS_TRY(h->rot.ensure((size_t)2 * std::max<int64_t>(p, 1) * (m - 1 + 1) * sizeof(double)));
-  GS_TRY(h->invw.ensure((size_t)5 * m * s * sizeof(double)));
+  GS_TRY(h->invw.ensure((size_t)5 * m * k * sizeof(double)));
   GS_TRY(h->state.ensure(sizeof(LanczosState)));
   double *V = h->V.d();
+  // ke1 operator: C's lower triangle as fp32 hi/lo tiles (default) or C itself
+  h->use_df = (h->opts.fp64_symv == 0);
+  if (h->use_df) {
+    GS_TRY(h->dfop.ensure(df_operator_bytes(n)));
+    GS_TRY(h->dfpart.ensure(df_partials_bytes(n)));
+    h->op.hi = static_cast<float *>(h->dfop.p);
+    h->op.W = static_cast<float2 *>(h->dfpart.p);
+    const int64_t NTt = ceil_div(n, 64);
+    h->op.wsplit = h->op.W + (size_t)NTt * NTt * 64;
+    GS_TRY(df_operator_build(st, n, C, ldc, h->op));
+  }
   LanczosState *dstate = static_cast<LanczosState *>(h->state.p);
   LanczosState hs;
   std::memset(&hs, 0, sizeof(hs));
@@ -212,7 +287,11 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
   GS_TRY(lz_norm_finish(st, h->sq.d(), (int)np, dstate, nullptr));
   GS_TRY(lz_scale_into(st, n, h->z.d(), V, dstate));
 
+  const bool thick = (h->opts.qr_restart == 0);
+  int64_t ka = 0;                                               // arrow rows of M (thick restart)
   const int64_t wf = (which == GSYEIG_LARGEST) ? m - s : 0;  // first wanted index among the m Ritz values
+  const int64_t kfirst = (which == GSYEIG_LARGEST) ? m - k : 0;  // first kept index (thick restart)
+  const int64_t woff = (thick && which == GSYEIG_LARGEST) ? k - s : 0;  // wanted columns within S
   const double *shifts = (which == GSYEIG_LARGEST) ? h->theta.d() : h->theta.d() + k;
   const int dir = (which == GSYEIG_LARGEST) ? -1 : 1;  // nearest-to-wanted shift first
   int64_t j0 = 0, restarts = 0, matvecs = 0, breakdowns = 0;
@@ -235,9 +314,20 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
       continue;
     }
     // Ritz values of T_m, vectors of the wanted ones, convergence test
-    GS_TRY(tri_bisect(st, m, h->alpha.d(), h->beta.d(), 0, m, h->theta.d()));
-    GS_TRY(tri_invit(st, m, h->alpha.d(), h->beta.d(), s, h->theta.d() + wf, h->S.d(), m, h->invw.d()));
-    GS_TRY(tri_converged(st, m, s, h->theta.d(), h->beta.d(), h->S.d(), m, h->opts.tol, dstate));
+    {
+      ProfRegion pr(st, PROF_RITZ);
+      if (thick) {
+        // the k kept Ritz pairs (the s wanted among them); M has an arrow after a restart
+        GS_TRY(tri_bisect(st, m, h->alpha.d(), h->beta.d(), ka, h->arrow.d(), kfirst, k, h->theta.d()));
+        GS_TRY(tri_invit(st, m, h->alpha.d(), h->beta.d(), ka, h->arrow.d(), k, h->theta.d(), h->S.d(), m,
+                         h->invw.d()));
+      } else {
+        GS_TRY(tri_bisect(st, m, h->alpha.d(), h->beta.d(), 0, nullptr, 0, m, h->theta.d()));
+        GS_TRY(tri_invit(st, m, h->alpha.d(), h->beta.d(), 0, nullptr, s, h->theta.d() + wf, h->S.d(), m,
+                         h->invw.d()));
+      }
+      GS_TRY(tri_converged(st, m, s, h->theta.d(), h->beta.d(), h->S.d() + (size_t)woff * m, m, h->opts.tol, dstate));
+    }
     GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
     if (hs.nconv >= s) break;
@@ -252,28 +342,42 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
         break;
       }
     }
-    // implicit restart with the p unwanted Ritz values as exact shifts
-    GS_TRY(tri_qr_shifts(st, m, p, h->alpha.d(), h->beta.d(), shifts, dir, h->alphaP.d(), h->betaP.d(), h->Q.d(), m,
-                         h->rot.d()));
-    GS_TRY(dgemm(st, false, false, n, k + 1, m, 1.0, V, n, h->Q.d(), m, 0.0, h->Vq.d(), n));
-    GS_TRY(lz_restart_residual(st, n, k, m, h->Vq.d(), n, V + (size_t)m * n, h->betaP.d(), h->beta.d(), h->Q.d(), m,
-                               h->z.d()));
-    GS_TRY(copy_block(st, n, k, h->Vq.d(), n, V, n));
-    GS_CUDA(cudaMemcpyAsync(h->alpha.p, h->alphaP.p, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    GS_CUDA(cudaMemcpyAsync(h->beta.p, h->betaP.p, (size_t)(k - 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    GS_CUDA(cudaMemsetAsync(h->beta.d() + k, 0, (size_t)(m - k) * sizeof(double), st));
-    // clean the new residual against V_k (CGS2), beta_{k-1} = ||f||, v_k = f / ||f||
-    GS_TRY(lz_cgs2(st, n, k, V, n, h->z.d(), h->h1.d(), h->h2.d(), h->sq.d()));
-    GS_TRY(lz_norm_finish(st, h->sq.d(), (int)np, dstate, h->beta.d() + (k - 1)));
-    GS_TRY(lz_scale_into(st, n, h->z.d(), V + (size_t)k * n, dstate));
+    ProfRegion pr(st, PROF_RESTART);
+    if (thick) {
+      // thick restart (same Krylov subspace and projection as the exact-shift
+      // implicit restart): keep the k Ritz vectors, continue from v_m
+      GS_TRY(dgemm(st, false, false, n, k, m, 1.0, V, n, h->S.d(), m, 0.0, h->Vq.d(), n));
+      GS_TRY(copy_block(st, n, k, h->Vq.d(), n, V, n));
+      GS_CUDA(cudaMemcpyAsync(V + (size_t)k * n, V + (size_t)m * n, (size_t)n * sizeof(double),
+                              cudaMemcpyDeviceToDevice, st));
+      GS_TRY(lz_thick_restart(st, m, k, h->theta.d(), h->S.d(), h->alpha.d(), h->beta.d(), h->arrow.d()));
+      ka = k;
+    } else {
+      // implicit restart with the p unwanted Ritz values as exact shifts
+      GS_TRY(tri_qr_shifts(st, m, p, h->alpha.d(), h->beta.d(), shifts, dir, h->alphaP.d(), h->betaP.d(), h->Q.d(),
+                           m, h->rot.d()));
+      GS_TRY(dgemm(st, false, false, n, k + 1, m, 1.0, V, n, h->Q.d(), m, 0.0, h->Vq.d(), n));
+      GS_TRY(lz_restart_residual(st, n, k, m, h->Vq.d(), n, V + (size_t)m * n, h->betaP.d(), h->beta.d(), h->Q.d(),
+                                 m, h->z.d()));
+      GS_TRY(copy_block(st, n, k, h->Vq.d(), n, V, n));
+      GS_CUDA(cudaMemcpyAsync(h->alpha.p, h->alphaP.p, (size_t)k * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      GS_CUDA(
+          cudaMemcpyAsync(h->beta.p, h->betaP.p, (size_t)(k - 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      GS_CUDA(cudaMemsetAsync(h->beta.d() + k, 0, (size_t)(m - k) * sizeof(double), st));
+      // clean the new residual against V_k (CGS2), beta_{k-1} = ||f||, v_k = f / ||f||
+      GS_TRY(lz_cgs2(st, n, k, V, n, h->z.d(), h->h1.d(), h->h2.d(), h->sq.d()));
+      GS_TRY(lz_norm_finish(st, h->sq.d(), (int)np, dstate, h->beta.d() + (k - 1)));
+      GS_TRY(lz_scale_into(st, n, h->z.d(), V + (size_t)k * n, dstate));
+    }
     restarts++;
     j0 = k;
   }
   // ke3: Ritz vectors Y = V_m S
   cudaEvent_t e0 = h->ev[5], e1 = h->ev[6];
   GS_CUDA(cudaEventRecord(e0, st));
-  GS_TRY(dgemm(st, false, false, n, s, m, 1.0, V, n, h->S.d(), m, 0.0, Y, ldy));
-  GS_CUDA(cudaMemcpyAsync(theta_out, h->theta.d() + wf, (size_t)s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  GS_TRY(dgemm(st, false, false, n, s, m, 1.0, V, n, h->S.d() + (size_t)woff * m, m, 0.0, Y, ldy));
+  GS_CUDA(cudaMemcpyAsync(theta_out, h->theta.d() + (thick ? woff : wf), (size_t)s * sizeof(double),
+                          cudaMemcpyDeviceToDevice, st));
   GS_CUDA(cudaEventRecord(e1, st));
   GS_CUDA(cudaEventSynchronize(e1));
   if (ms_ke3) *ms_ke3 = elapsed(e0, e1);
@@ -349,7 +453,7 @@ int gsyeig_destroy(gsyeig_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
-  DevBuf *bufs[] = {&h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
+  DevBuf *bufs[] = {&h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
                     &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
                     &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
   for (DevBuf *b : bufs) b->release();
@@ -365,7 +469,9 @@ int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
   if (!h) return -1;
   if (!o) return -2;
   if (!(o->tol > 0.0) || o->krylov_dim < 0 || o->keep < 0 || o->max_restarts < 0 || o->timeout_ms < 0 ||
-      o->block < 0 || o->block > 160 || (o->block > 0 && o->block < 16) || o->profile < 0 || o->profile > 1)
+      o->block < 0 || o->block > 160 || (o->block > 0 && o->block < 16) || o->profile < 0 || o->profile > 1 ||
+      o->fp64_gemm < 0 || o->fp64_gemm > 2 || o->fp64_symv < 0 || o->fp64_symv > 1 || o->qr_restart < 0 ||
+      o->qr_restart > 1 || o->reserved != 0)
     return -2;
   if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
   h->opts = *o;
@@ -395,6 +501,7 @@ int gsyeig_potrf(gsyeig_handle h, double *dB, int64_t ldb, int64_t n, int64_t *p
   if (ldb < std::max<int64_t>(1, n)) return -3;
   if (n < 1) return -4;
   GS_TRY(begin(h));
+  GemmScope gscope;
   const int nb = nb_of(h, n);
   FactorWork w;
   GS_TRY(factor_ws(h, n, nb, 1, w));
@@ -402,6 +509,7 @@ int gsyeig_potrf(gsyeig_handle h, double *dB, int64_t ldb, int64_t n, int64_t *p
   int flag = 0;
   GS_CUDA(cudaMemcpyAsync(&flag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   GS_TRY(finish(h));
+  GS_TRY(gemm_check(h));
   if (potrf_index) *potrf_index = flag;
   return flag ? GSYEIG_NOT_SPD : GSYEIG_SUCCESS;
 }
@@ -414,11 +522,13 @@ int gsyeig_sygst(gsyeig_handle h, double *dA, int64_t lda, const double *dU, int
   if (ldu < std::max<int64_t>(1, n)) return -5;
   if (n < 1) return -6;
   GS_TRY(begin(h));
+  GemmScope gscope;
   const int nb = nb_of(h, n);
   FactorWork w;
   GS_TRY(factor_ws(h, n, nb, 1, w));
   GS_TRY(sygst_blocked(h->st, n, dA, lda, dU, ldu, nb, w, false));
-  return finish(h);
+  GS_TRY(finish(h));
+  return gemm_check(h);
 }
 
 int gsyeig_symv(gsyeig_handle h, const double *dC, int64_t ldc, int64_t n, const double *dw, double *dz) {
@@ -442,11 +552,13 @@ int gsyeig_trsm_back(gsyeig_handle h, const double *dU, int64_t ldu, int64_t n, 
   if (ldy < n) return -6;
   if (s < 1) return -7;
   GS_TRY(begin(h));
+  GemmScope gscope;
   const int nb = nb_of(h, n);
   FactorWork w;
   GS_TRY(factor_ws(h, n, nb, s, w));
   GS_TRY(trsm_back_blocked(h->st, n, dU, ldu, dY, ldy, s, nb, w, false));
-  return finish(h);
+  GS_TRY(finish(h));
+  return gemm_check(h);
 }
 
 int gsyeig_tridiag_eig(gsyeig_handle h, const double *d, const double *e, int64_t m, int64_t first, int64_t cnt,
@@ -460,10 +572,10 @@ int gsyeig_tridiag_eig(gsyeig_handle h, const double *d, const double *e, int64_
   if (!lam) return -7;
   if (dZ && ldz < m) return -9;
   GS_TRY(begin(h));
-  GS_TRY(tri_bisect(h->st, m, d, e, first, cnt, lam));
+  GS_TRY(tri_bisect(h->st, m, d, e, 0, nullptr, first, cnt, lam));
   if (dZ) {
     GS_TRY(h->invw.ensure((size_t)5 * m * cnt * sizeof(double)));
-    GS_TRY(tri_invit(h->st, m, d, e, cnt, lam, dZ, ldz, h->invw.d()));
+    GS_TRY(tri_invit(h->st, m, d, e, 0, nullptr, cnt, lam, dZ, ldz, h->invw.d()));
   }
   return finish(h);
 }
@@ -487,6 +599,8 @@ int gsyeig_syev_lanczos(gsyeig_handle h, const double *dC, int64_t ldc, int64_t 
   const int64_t l0 = g_launches.load();
   GS_TRY(begin(h));
   ProfScope prof(h);
+  GemmScope gscope;
+  current_gemm() = nullptr;  // the Lanczos stage's GEMMs have K = m > 128: FP64 engine
   GS_TRY(h->hw.ensure((size_t)s * sizeof(double)));
   double ms_ke3 = 0;
   cudaEventRecord(h->ev[0], h->st);
@@ -518,6 +632,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   const int64_t l0 = g_launches.load();
   GS_TRY(begin(h));
   ProfScope prof(h);
+  GemmScope gscope;
   cudaStream_t st = h->st;
   // host inputs: stage them in the handle's device buffers
   const bool hostA = !is_device_ptr(A), hostB = !is_device_ptr(B), hostX = !is_device_ptr(X);
@@ -569,6 +684,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
                               cudaMemcpyDeviceToHost, st));
   GS_CUDA(cudaEventRecord(h->ev[8], st));
   GS_TRY(finish(h));
+  GS_TRY(gemm_check(h));
   prof.fill(info);
   if (info) {
     info->ms_gs1 = elapsed(h->ev[1], h->ev[2]);

@@ -157,6 +157,19 @@ __global__ void k_restart_residual(int64_t n, int64_t k, int64_t m, const double
     f[i] = vk[i] * c1 + vm[i] * c2;
 }
 
+__global__ void k_thick_restart(int64_t m, int64_t k, const double *theta, const double *S, double *d, double *e,
+                                double *b) {
+  const double bm = e[m - 1];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+    b[i] = bm * S[(m - 1) + (size_t)i * m];
+    d[i] = theta[i];
+  }
+}
+
+__global__ void k_zero(int64_t n, double *p) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0.0;
+}
+
 unsigned grid1d(int64_t n, int threads) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), 152 * 8)); }
 
 }  // namespace
@@ -221,6 +234,16 @@ int lz_norm_finish(cudaStream_t st, const double *sq, int nparts, LanczosState *
 int lz_random(cudaStream_t st, int64_t n, uint64_t seed, uint64_t stream, double *v) {
   k_random<<<grid1d(n, 256), 256, 0, st>>>(n, seed, stream, v);
   count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int lz_thick_restart(cudaStream_t st, int64_t m, int64_t k, const double *theta, const double *S, double *d, double *e,
+                     double *b) {
+  // b and d first (they read e[m - 1]); the couplings e[0..k-1] are then cleared
+  k_thick_restart<<<grid1d(k, 256), 256, 0, st>>>(m, k, theta, S, d, e, b);
+  k_zero<<<grid1d(k, 256), 256, 0, st>>>(k, e);
+  count_launch(2);
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
 }

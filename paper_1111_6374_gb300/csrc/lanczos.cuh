@@ -30,25 +30,35 @@ int lz_finalize(cudaStream_t st, int64_t j, int64_t m, const double *h1, const d
 int lz_scale_into(cudaStream_t st, int64_t n, const double *z, double *out, const LanczosState *state);
 int lz_norm_finish(cudaStream_t st, const double *sq, int nparts, LanczosState *state, double *norm_out);
 int lz_random(cudaStream_t st, int64_t n, uint64_t seed, uint64_t stream, double *v);
+// Thick restart bookkeeping: d[i] = theta[i], arrow b[i] = beta[m-1] S[m-1, i]
+// and e[i] = 0 for i < k (S is m x k, ld m).
+int lz_thick_restart(cudaStream_t st, int64_t m, int64_t k, const double *theta, const double *S, double *d, double *e,
+                     double *b);
 int lz_restart_residual(cudaStream_t st, int64_t n, int64_t k, int64_t m, const double *Vq, int64_t ldvq,
                         const double *vm, const double *betaP, const double *beta, const double *Q, int64_t ldq,
                         double *f);
 
 // --- tridiag.cu -------------------------------------------------------------
-// Eigenvalues with ascending indices first..first+cnt-1 of (d, e) by bisection.
-int tri_bisect(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t first, int64_t cnt, double *lam);
-// Unit eigenvectors (m x cnt, ldz) for ascending eigenvalues lam by inverse
-// iteration; eigenvalues closer than 1e-10 ||T|| are orthogonalised as a
-// cluster.  work: cnt * 5m doubles.
-int tri_invit(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t cnt, const double *lam,
-              double *Z, int64_t ldz, double *work);
+// The small symmetric matrices M of the Lanczos stage: diagonal d[0..m-1];
+// rows i < ka couple only to row ka, through b[i] (the "arrow" left by a
+// thick restart; ka = 0, b = NULL for a plain tridiagonal); rows i >= ka are
+// tridiagonal with e[i] coupling rows i and i+1.
+// Eigenvalues with ascending indices first..first+cnt-1 of M by bisection.
+int tri_bisect(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t ka, const double *b, int64_t first,
+               int64_t cnt, double *lam);
+// Unit eigenvectors (m x cnt, ldz) of M for ascending eigenvalues lam by
+// inverse iteration; eigenvalues closer than 1e-10 ||M|| are orthogonalised
+// as a cluster.  work: cnt * 5m doubles.
+int tri_invit(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t ka, const double *b, int64_t cnt,
+              const double *lam, double *Z, int64_t ldz, double *work);
 // p = m - k exact-shift implicit QR steps on T_m (alpha, beta); shift i is
 // shifts[i] (dir > 0) or shifts[p - 1 - i] (dir < 0).  Writes the
 // transformed T into (alphaP, betaP) and the accumulated orthogonal Q
 // (m x m, ldq).  rot: 2 p (m - 1) doubles of rotation scratch.
 int tri_qr_shifts(cudaStream_t st, int64_t m, int64_t p, const double *alpha, const double *beta,
                   const double *shifts, int dir, double *alphaP, double *betaP, double *Q, int64_t ldq, double *rot);
-// Convergence test of the wanted Ritz pairs: estimate_i = |beta[m-1] Z[m-1, i]|.
+// Convergence test of the wanted Ritz pairs: estimate_i = |beta[m-1] Z[m-1, i]|
+// relative to the running ||T|| estimate state->tnorm.
 int tri_converged(cudaStream_t st, int64_t m, int64_t cnt, const double *theta_all, const double *beta,
                   const double *Z, int64_t ldz, double tol, LanczosState *state);
 

@@ -1,0 +1,233 @@
+// ke1 on the FP32 pipes: z = C w with C held as a pair of fp32 matrices
+// (C = C_hi + C_lo to about 2^-48 relative per entry) and only its lower
+// triangle stored, in 64 x 64 tiles.
+//
+// In FP64 the product is bound by GB300's FP64 pipe (2n^2 flops at ~1.26
+// TFLOP/s, 0.43 ms at n = 16384), not by HBM.  Here every product of
+// (c_hi + c_lo)(w_hi + w_lo) is formed with an error-free product on the
+// fp32 pipe and summed with compensated (twice-working-precision) dot
+// products (Ogita, Rump, Oishi, "Accurate sum and dot product", 2005), so
+// the operator applied is C_hi + C_lo to ~2^-48 and each 64-term partial is
+// accurate to ~2^-48; partials are combined in double-float and rounded to
+// FP64 once per row.  The stored bytes are
+// 4 n(n+1)/2 * 2 = half of the full FP64 square, and each stored tile is
+// used twice (C_ij w_j and C_ij^T w_i): the kernel is HBM-bound.
+//
+// Layout: tile t = bi (bi + 1) / 2 + bj for bi >= bj; within a tile,
+// element (r, c) at r + 64 c (column-major); hi and lo in two arrays.
+// Diagonal tiles hold the full symmetric 64 x 64 block.  Partials go to
+// W[slot][row]: tile (bi, bj) writes its row sums to slot bj of rows in
+// block bi and (off-diagonal) its column sums to slot bi of rows in block
+// bj, so each (slot, row) is written exactly once; a second kernel sums the
+// NT slots of every row in double-float.  Deterministic.
+#include "symv_df.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int TS = 64;           // tile size
+constexpr int DF_THREADS = 256;  // 8 warps: rows lane + 32 (warp & 1), column group warp >> 1
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (s, c) += (p, e): compensated accumulation of a product given as p + e
+__device__ __forceinline__ void acc2(float &s, float &c, float p, float e) {
+  float t, q;
+  two_sum(s, p, t, q);
+  s = t;
+  c += q + e;
+}
+
+__global__ void k_op_build(int64_t n, int64_t NT, const double *__restrict__ C, int64_t ldc, float *__restrict__ hi,
+                           float *__restrict__ lo) {
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  const int64_t t = bi * (bi + 1) / 2 + bj;
+  float *h = hi + t * TS * TS, *l = lo + t * TS * TS;
+  for (int idx = threadIdx.x; idx < TS * TS; idx += blockDim.x) {
+    const int r = idx % TS, c = idx / TS;
+    const int64_t i = bi * TS + r, j = bj * TS + c;
+    double v = 0.0;
+    if (i < n && j < n) v = C[i + j * ldc];
+    const float vh = (float)v;
+    h[idx] = vh;
+    l[idx] = (float)(v - (double)vh);
+  }
+}
+
+__global__ void k_vec_split(int64_t n, int64_t npad, const double *__restrict__ w, float2 *__restrict__ ws) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (i < n) ? w[i] : 0.0;
+    const float vh = (float)v;
+    ws[i] = make_float2(vh, (float)(v - (double)vh));
+  }
+}
+
+// (bi, bj) of packed tile t; fp32 estimate (GB300's FP64 pipe is slow)
+// corrected by integer steps.
+__device__ __forceinline__ void tile_of(int64_t t, int64_t &bi, int64_t &bj) {
+  int64_t b = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (b * (b + 1) / 2 > t) b--;
+  while ((b + 1) * (b + 2) / 2 <= t) b++;
+  bi = b;
+  bj = t - b * (b + 1) / 2;
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, q;
+  two_sum(a.x, b.x, s, q);
+  return make_float2(s, a.y + b.y + q);
+}
+
+__global__ void __launch_bounds__(DF_THREADS) k_symv_df(int64_t NT, int64_t npad, const float *__restrict__ hi,
+                                                        const float *__restrict__ lo, const float2 *__restrict__ ws,
+                                                        float2 *__restrict__ W) {
+  __shared__ float2 xr[TS], xc[TS];  // w of the tile's column block (row sums), row block (col sums)
+  __shared__ float2 rowp[4][TS];     // row-sum partials of the 4 column groups
+  __shared__ float2 colp[2][TS];     // column-sum partials of the 2 row halves
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = lane + 32 * (warp & 1), g = warp >> 1;  // row, column group (16 columns)
+  const int64_t ntiles = NT * (NT + 1) / 2;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int64_t bi, bj;
+    tile_of(t, bi, bj);
+    const bool diag = (bi == bj);
+    if (threadIdx.x < TS) xr[threadIdx.x] = ws[bj * TS + threadIdx.x];
+    else if (threadIdx.x < 2 * TS) xc[threadIdx.x - TS] = ws[bi * TS + threadIdx.x - TS];
+    __syncthreads();
+    const float *h = hi + t * TS * TS, *l = lo + t * TS * TS;
+    float ch[16], cl[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const int c = g * 16 + k;
+      ch[k] = __ldg(&h[r + TS * c]);
+      cl[k] = __ldg(&l[r + TS * c]);
+    }
+    // row sums over this thread's 16 columns (compensated dot product)
+    float rs = 0.f, rc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      const float2 x = xr[g * 16 + k];
+      float p, e;
+      two_prod(ch[k], x.x, p, e);
+      e = fmaf(ch[k], x.y, e);
+      e = fmaf(cl[k], x.x, e);
+      acc2(rs, rc, p, e);
+    }
+    rowp[g][r] = make_float2(rs, rc);
+    if (!diag) {
+      // column sums: products c_rk * w_r, reduced over the 32 lanes by
+      // recursive halving (lane l ends up owning column g*16 + (l >> 1))
+      const float2 xi = xc[r];
+      float2 v[16];
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        float p, e;
+        two_prod(ch[k], xi.x, p, e);
+        e = fmaf(ch[k], xi.y, e);
+        e = fmaf(cl[k], xi.x, e);
+        v[k] = make_float2(p, e);
+      }
+#pragma unroll
+      for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < half; k++) {
+          const float2 keep = up ? v[k + half] : v[k];
+          const float2 give = up ? v[k] : v[k + half];
+          float2 got;
+          got.x = __shfl_xor_sync(0xffffffffu, give.x, o);
+          got.y = __shfl_xor_sync(0xffffffffu, give.y, o);
+          v[k] = df_add(keep, got);
+        }
+      }
+      float2 other;
+      other.x = __shfl_xor_sync(0xffffffffu, v[0].x, 1);
+      other.y = __shfl_xor_sync(0xffffffffu, v[0].y, 1);
+      if ((lane & 1) == 0) colp[warp & 1][g * 16 + (lane >> 1)] = df_add(v[0], other);
+    }
+    __syncthreads();
+    if (threadIdx.x < TS) {
+      // rows of block bi: combine the 4 column groups
+      const int rr = threadIdx.x;
+      float2 a = df_add(df_add(rowp[0][rr], rowp[1][rr]), df_add(rowp[2][rr], rowp[3][rr]));
+      W[bj * npad + bi * TS + rr] = a;
+    } else if (!diag && threadIdx.x < 2 * TS) {
+      const int cc = threadIdx.x - TS;
+      W[bi * npad + bj * TS + cc] = df_add(colp[0][cc], colp[1][cc]);
+    }
+    __syncthreads();
+  }
+}
+
+// z_i = sum over the NT slots of W[slot][i], accumulated in double-float and
+// rounded to FP64 once.
+__global__ void k_reduce_slots(int64_t n, int64_t npad, int64_t NT, const float2 *__restrict__ W, double *__restrict__ z) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    int64_t q = 0;
+    for (; q + 1 < NT; q += 2) {
+      a = df_add(a, W[q * npad + i]);
+      b = df_add(b, W[(q + 1) * npad + i]);
+    }
+    if (q < NT) a = df_add(a, W[q * npad + i]);
+    a = df_add(a, b);
+    z[i] = (double)a.x + (double)a.y;
+  }
+}
+
+}  // namespace
+
+size_t df_operator_bytes(int64_t n) {
+  const int64_t NT = ceil_div(n, TS);
+  return (size_t)NT * (NT + 1) / 2 * TS * TS * sizeof(float) * 2;
+}
+
+size_t df_partials_bytes(int64_t n) {
+  const int64_t NT = ceil_div(n, TS);
+  return (size_t)NT * NT * TS * sizeof(float2) + (size_t)NT * TS * sizeof(float2);
+}
+
+int df_operator_build(cudaStream_t st, int64_t n, const double *C, int64_t ldc, DfOperator &op) {
+  const int64_t NT = ceil_div(n, TS);
+  op.n = n;
+  op.NT = NT;
+  op.npad = NT * TS;
+  const size_t tiles = (size_t)NT * (NT + 1) / 2 * TS * TS;
+  op.lo = op.hi + tiles;
+  k_op_build<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, NT, C, ldc, op.hi, op.lo);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int df_symv(cudaStream_t st, const DfOperator &op, const double *w, double *z) {
+  KernelProfiler *prof = current_profiler();
+  size_t e0 = prof ? prof->start(st) : SIZE_MAX;
+  const int64_t ntiles = op.NT * (op.NT + 1) / 2;
+  k_vec_split<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.npad, 256), 1024)), 256, 0, st>>>(
+      op.n, op.npad, w, op.wsplit);
+  k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, 152 * 8), DF_THREADS, 0, st>>>(op.NT, op.npad, op.hi, op.lo,
+                                                                                 op.wsplit, op.W);
+  k_reduce_slots<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.n, 256), 1024)), 256, 0, st>>>(
+      op.n, op.npad, op.NT, op.W, z);
+  count_launch(3);
+  GS_CHECK_LAUNCH();
+  if (prof) {
+    const double n = (double)op.n;
+    // algorithmic: 2n^2 flops; the stored triangle (hi + lo, 8 bytes per entry of n(n+1)/2) plus w and z
+    prof->stop(st, e0, PROF_SYMV, 2.0 * n * n, 8.0 * (n * (n + 1) / 2) + 16.0 * n);
+  }
+  return GSYEIG_SUCCESS;
+}
+
+}  // namespace gs

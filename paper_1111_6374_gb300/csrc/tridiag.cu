@@ -25,13 +25,26 @@ constexpr int BIS_THREADS = 128;
 
 __device__ __forceinline__ double sturm_pivmin(double maxe2) { return DBL_MIN * fmax(1.0, maxe2); }
 
-// Number of eigenvalues of (d, e2 = e^2) strictly below x.
-__device__ int64_t sturm_below(int64_t m, const double *d, const double *e2, double x, double pivmin) {
+// Number of eigenvalues strictly below x of the symmetric matrix M with
+// diagonal d, arrow couplings b[0..ka-1] between rows i < ka and row ka, and
+// tridiagonal couplings e[i] (i >= ka) between rows i and i+1 (e2 = e^2,
+// b2 = b^2).  ka = 0 is a plain tridiagonal.  Inertia of M - x I by block
+// elimination in the order 0, 1, ..., m-1 (Sylvester): the arrow rows are
+// diagonal, so their pivots are d_i - x and they only update row ka.
+__device__ int64_t sturm_below(int64_t m, int64_t ka, const double *d, const double *e2, const double *b2, double x,
+                               double pivmin) {
   int64_t cnt = 0;
-  double q = d[0] - x;
+  double acc = 0.0;
+  for (int64_t i = 0; i < ka; i++) {
+    double p = d[i] - x;
+    if (fabs(p) < pivmin) p = -pivmin;
+    if (p < 0.0) cnt++;
+    acc += b2[i] / p;
+  }
+  double q = (d[ka] - x) - acc;
   if (fabs(q) < pivmin) q = -pivmin;
   if (q < 0.0) cnt++;
-  for (int64_t i = 1; i < m; i++) {
+  for (int64_t i = ka + 1; i < m; i++) {
     q = (d[i] - x) - e2[i - 1] / q;
     if (fabs(q) < pivmin) q = -pivmin;
     if (q < 0.0) cnt++;
@@ -56,23 +69,39 @@ __device__ void block_minmax(double &lo, double &hi, double *sh) {
   __syncthreads();
 }
 
-// dynamic smem: d[m], e2[m], scratch[2*blockDim]
+// dynamic smem: d[m], e2[m], b2[m], scratch[2*blockDim]
 __global__ void __launch_bounds__(BIS_THREADS) k_bisect(int64_t m, const double *__restrict__ d,
-                                                        const double *__restrict__ e, int64_t first, int64_t cnt,
+                                                        const double *__restrict__ e, int64_t ka,
+                                                        const double *__restrict__ b, int64_t first, int64_t cnt,
                                                         double *__restrict__ lam) {
   extern __shared__ double sm[];
-  double *ds = sm, *e2 = sm + m, *sh = sm + 2 * m;
-  double lo = DBL_MAX, hi = -DBL_MAX, me2 = 0.0;
+  double *ds = sm, *e2 = sm + m, *b2 = sm + 2 * m, *sh = sm + 3 * m;
+  double lo = DBL_MAX, hi = -DBL_MAX, me2 = 0.0, bsum = 0.0;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-    double di = d[i];
-    double el = (i > 0) ? fabs(e[i - 1]) : 0.0, er = (i + 1 < m) ? fabs(e[i]) : 0.0;
+    const double di = d[i];
+    // couplings of row i: arrow rows have only b_i; row ka has all b plus e[ka]; others e[i-1], e[i]
+    const double el = (i > ka) ? fabs(e[i - 1]) : 0.0, er = (i >= ka && i + 1 < m) ? fabs(e[i]) : 0.0;
+    const double bi = (i < ka) ? fabs(b[i]) : 0.0;
     ds[i] = di;
-    e2[i] = (i + 1 < m) ? e[i] * e[i] : 0.0;
-    me2 = fmax(me2, er * er);
-    lo = fmin(lo, di - el - er);
-    hi = fmax(hi, di + el + er);
+    e2[i] = (i >= ka && i + 1 < m) ? e[i] * e[i] : 0.0;
+    b2[i] = (i < ka) ? b[i] * b[i] : 0.0;
+    me2 = fmax(me2, fmax(er * er, bi * bi));
+    bsum += bi;
+    lo = fmin(lo, di - el - er - bi);
+    hi = fmax(hi, di + el + er + bi);
   }
   block_minmax(lo, hi, sh);
+  // row ka also carries the sum of all arrow couplings
+  __shared__ double s_bsum;
+  if (threadIdx.x == 0) s_bsum = 0.0;
+  __syncthreads();
+  atomicAdd(&s_bsum, bsum);
+  __syncthreads();
+  if (ka > 0) {
+    const double dk = d[ka], ek = (ka + 1 < m) ? fabs(e[ka]) : 0.0;
+    lo = fmin(lo, dk - s_bsum - ek);
+    hi = fmax(hi, dk + s_bsum + ek);
+  }
   double tmp = -me2, dummy = 0.0;
   block_minmax(tmp, dummy, sh);
   me2 = -tmp;
@@ -83,16 +112,16 @@ __global__ void __launch_bounds__(BIS_THREADS) k_bisect(int64_t m, const double 
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
   const int64_t q = first + t;  // 0-based index of the wanted eigenvalue
-  double a = lo, b = hi;
+  double xa = lo, xb = hi;
   for (int it = 0; it < 256; it++) {
-    double mid = 0.5 * (a + b);
-    if (b - a <= 2.0 * DBL_EPSILON * fmax(fabs(a), fabs(b)) + 4.0 * pivmin || mid == a || mid == b) break;
-    if (sturm_below(m, ds, e2, mid, pivmin) > q)
-      b = mid;
+    const double mid = 0.5 * (xa + xb);
+    if (xb - xa <= 2.0 * DBL_EPSILON * fmax(fabs(xa), fabs(xb)) + 4.0 * pivmin || mid == xa || mid == xb) break;
+    if (sturm_below(m, ka, ds, e2, b2, mid, pivmin) > q)
+      xb = mid;
     else
-      a = mid;
+      xa = mid;
   }
-  lam[t] = 0.5 * (a + b);
+  lam[t] = 0.5 * (xa + xb);
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -103,26 +132,48 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   return x ^ (x >> 33);
 }
 
-// Inverse iteration, one thread per eigenvalue.  Elimination of T - lam I
-// row by row with partial pivoting between the running row and the next
-// original row; U has two superdiagonals.  Work per thread: 5m doubles.
-__global__ void k_invit(int64_t m, const double *__restrict__ d, const double *__restrict__ e, int64_t cnt,
-                        const double *__restrict__ lam, double *__restrict__ Z, int64_t ldz, double *__restrict__ work) {
+// Inverse iteration, one thread per eigenvalue, on M - lam I with M as in
+// sturm_below (arrow rows 0..ka-1, tridiagonal from row ka).  The arrow rows
+// are eliminated first (pivots d_i - lam), which only changes the diagonal
+// and right-hand side of row ka; the remaining tridiagonal rows ka..m-1 are
+// eliminated with partial pivoting between the running row and the next
+// original row (U gets two superdiagonals).  Tiny pivots are replaced by
+// eps ||M||, the classical device that makes the solve return the wanted
+// direction.  Work per thread: 5m doubles.
+__global__ void k_invit(int64_t m, const double *__restrict__ d, const double *__restrict__ e, int64_t ka,
+                        const double *__restrict__ b, int64_t cnt, const double *__restrict__ lam,
+                        double *__restrict__ Z, int64_t ldz, double *__restrict__ work) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt) return;
   double *p0 = work + (size_t)t * 5 * m, *p1 = p0 + m, *p2 = p1 + m, *mu = p2 + m, *sw = mu + m;
   double *z = Z + (size_t)t * ldz;
-  double tn = 0.0;
+  double tn = 0.0, bs = 0.0;
   for (int64_t i = 0; i < m; i++) {
-    double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < m ? fabs(e[i]) : 0.0);
+    double r = fabs(d[i]);
+    if (i < ka) {
+      r += fabs(b[i]);
+      bs += fabs(b[i]);
+    } else {
+      if (i > ka) r += fabs(e[i - 1]);
+      if (i + 1 < m) r += fabs(e[i]);
+    }
     tn = fmax(tn, r);
   }
+  tn = fmax(tn, fabs(d[ka]) + bs + ((ka + 1 < m) ? fabs(e[ka]) : 0.0));
   if (tn == 0.0) tn = 1.0;
   const double tiny = DBL_EPSILON * tn;
   const double x = lam[t];
-  // factor
-  double a = d[0] - x, b = (m > 1) ? e[0] : 0.0, c = 0.0;
-  for (int64_t i = 0; i < m; i++) {
+  // arrow pivots and the Schur complement on row ka
+  double a = d[ka] - x;
+  for (int64_t i = 0; i < ka; i++) {
+    double piv = d[i] - x;
+    if (fabs(piv) < tiny) piv = copysign(tiny, piv);
+    p0[i] = piv;
+    a -= b[i] * b[i] / piv;
+  }
+  // factor rows ka..m-1
+  double bb = (ka + 1 < m) ? e[ka] : 0.0, c = 0.0;
+  for (int64_t i = ka; i < m; i++) {
     if (i == m - 1) {
       p0[i] = (fabs(a) < tiny) ? copysign(tiny, a) : a;
       p1[i] = p2[i] = mu[i] = sw[i] = 0.0;
@@ -132,26 +183,31 @@ __global__ void k_invit(int64_t m, const double *__restrict__ d, const double *_
     if (fabs(a) >= fabs(lo)) {
       const double piv = (fabs(a) < tiny) ? copysign(tiny, a) : a;
       const double f = lo / piv;
-      p0[i] = piv; p1[i] = b; p2[i] = c; mu[i] = f; sw[i] = 0.0;
-      a = nd - f * b;
-      b = nu - f * c;
+      p0[i] = piv; p1[i] = bb; p2[i] = c; mu[i] = f; sw[i] = 0.0;
+      a = nd - f * bb;
+      bb = nu - f * c;
     } else {
       const double f = a / lo;
       p0[i] = lo; p1[i] = nd; p2[i] = nu; mu[i] = f; sw[i] = 1.0;
-      a = b - f * nd;
-      b = c - f * nu;
+      a = bb - f * nd;
+      bb = c - f * nu;
     }
     c = 0.0;
   }
   // start vector
-  for (int64_t i = 0; i < m; i++) z[i] = 1.0 + 0.25 * ((double)(mix64((uint64_t)i * 0x9E3779B97F4A7C15ull + (uint64_t)t) >> 11) * 0x1p-53 - 0.5);
+  for (int64_t i = 0; i < m; i++)
+    z[i] = 1.0 + 0.25 * ((double)(mix64((uint64_t)i * 0x9E3779B97F4A7C15ull + (uint64_t)t) >> 11) * 0x1p-53 - 0.5);
   for (int it = 0; it < 3; it++) {
-    for (int64_t i = 0; i + 1 < m; i++) {
+    // arrow elimination on the right-hand side
+    double acc = 0.0;
+    for (int64_t i = 0; i < ka; i++) acc += b[i] * z[i] / p0[i];
+    z[ka] -= acc;
+    for (int64_t i = ka; i + 1 < m; i++) {
       if (sw[i] != 0.0) { double q = z[i]; z[i] = z[i + 1]; z[i + 1] = q; }
       z[i + 1] -= mu[i] * z[i];
     }
     double mx = 0.0;
-    for (int64_t i = m - 1; i >= 0; i--) {
+    for (int64_t i = m - 1; i >= ka; i--) {
       double v = z[i];
       if (i + 1 < m) v -= p1[i] * z[i + 1];
       if (i + 2 < m) v -= p2[i] * z[i + 2];
@@ -159,14 +215,20 @@ __global__ void k_invit(int64_t m, const double *__restrict__ d, const double *_
       z[i] = v;
       mx = fmax(mx, fabs(v));
     }
-    const double s = (mx > 0.0) ? 1.0 / mx : 1.0;
-    for (int64_t i = 0; i < m; i++) z[i] *= s;
+    const double xk = z[ka];
+    for (int64_t i = 0; i < ka; i++) {
+      const double v = (z[i] - b[i] * xk) / p0[i];
+      z[i] = v;
+      mx = fmax(mx, fabs(v));
+    }
+    const double sc = (mx > 0.0) ? 1.0 / mx : 1.0;
+    for (int64_t i = 0; i < m; i++) z[i] *= sc;
   }
   double nrm = 0.0;
   for (int64_t i = 0; i < m; i++) nrm = fma(z[i], z[i], nrm);
   nrm = sqrt(nrm);
-  const double s = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-  for (int64_t i = 0; i < m; i++) z[i] *= s;
+  const double sc = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+  for (int64_t i = 0; i < m; i++) z[i] *= sc;
 }
 
 __device__ double block_sum256(double v, double *red) {
@@ -288,7 +350,7 @@ __global__ void k_converged(int64_t m, int64_t cnt, const double *theta, const d
   __shared__ int64_t nc;
   if (threadIdx.x == 0) nc = 0;
   __syncthreads();
-  const double tn = fmax(fabs(theta[0]), fabs(theta[m - 1]));
+  const double tn = state->tnorm;  // running estimate of ||T|| from the recurrence
   const double bm = fabs(beta[m - 1]);
   double mx = 0.0;
   int64_t mine = 0;
@@ -313,22 +375,23 @@ __global__ void k_converged(int64_t m, int64_t cnt, const double *theta, const d
 
 }  // namespace
 
-int tri_bisect(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t first, int64_t cnt, double *lam) {
+int tri_bisect(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t ka, const double *b, int64_t first,
+               int64_t cnt, double *lam) {
   if (cnt <= 0) return GSYEIG_SUCCESS;
-  size_t smem = (size_t)(2 * m + 2 * BIS_THREADS) * sizeof(double);
+  size_t smem = (size_t)(3 * m + 2 * BIS_THREADS) * sizeof(double);
   if (smem > 48 * 1024)
     GS_CUDA(cudaFuncSetAttribute((const void *)k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_bisect<<<(unsigned)ceil_div(cnt, BIS_THREADS), BIS_THREADS, smem, st>>>(m, d, e, first, cnt, lam);
+  k_bisect<<<(unsigned)ceil_div(cnt, BIS_THREADS), BIS_THREADS, smem, st>>>(m, d, e, ka, b, first, cnt, lam);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
 }
 
-int tri_invit(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t cnt, const double *lam, double *Z,
-              int64_t ldz, double *work) {
+int tri_invit(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t ka, const double *b, int64_t cnt,
+              const double *lam, double *Z, int64_t ldz, double *work) {
   if (cnt <= 0) return GSYEIG_SUCCESS;
   // one thread per eigenvalue, spread over many SMs (32 threads per CTA)
-  k_invit<<<(unsigned)ceil_div(cnt, 32), 32, 0, st>>>(m, d, e, cnt, lam, Z, ldz, work);
+  k_invit<<<(unsigned)ceil_div(cnt, 32), 32, 0, st>>>(m, d, e, ka, b, cnt, lam, Z, ldz, work);
   count_launch();
   GS_CHECK_LAUNCH();
   k_cluster_orth<<<1, 256, 0, st>>>(m, cnt, lam, 0.0, d, e, Z, ldz);
@@ -421,10 +484,10 @@ extern "C" int gsyeig_tridiag_eig_noalloc(const double *d, const double *e, int6
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double *scratch = nullptr;
   if (dZ) GS_TRY(noalloc_scratch(&scratch));
-  GS_TRY(tri_bisect(st, m, d, e, first, cnt, lam));
+  GS_TRY(tri_bisect(st, m, d, e, 0, nullptr, first, cnt, lam));
   // inverse iteration writes every scratch entry before reading it, so the
   // previous call's contents need no clearing
-  if (dZ) GS_TRY(tri_invit(st, m, d, e, cnt, lam, dZ, ldz, scratch));
+  if (dZ) GS_TRY(tri_invit(st, m, d, e, 0, nullptr, cnt, lam, dZ, ldz, scratch));
   GS_CUDA(cudaStreamSynchronize(st));
   GS_CUDA(cudaGetLastError());
   return GSYEIG_SUCCESS;

@@ -31,6 +31,17 @@ def solver():
     return Solver(0)
 
 
+@pytest.fixture(scope="module", params=[0, 1, 2], ids=["tcgen05_sliced", "fp64_fma", "mma_sync_sliced"])
+def any_solver(request):
+    """The GEMM engines of gs1/gs2/bt1: bf16 tensor-core slicing on tcgen05
+    (default), plain FP64 FMA, and the same slicing on mma.sync."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1111_6374_gb300 import Solver
+
+    return Solver(0, fp64_gemm=request.param)
+
+
 def _np(t):
     return t.detach().cpu().numpy()
 
@@ -43,11 +54,11 @@ def _cm(a: np.ndarray) -> torch.Tensor:
 
 
 @pytest.mark.parametrize("n", [1, 37, 64, 200, 513, 1000])
-def test_potrf_matches_oracle(solver, n):
+def test_potrf_matches_oracle(any_solver, n):
     A, B, _ = inputs.make_pencil(max(n, 2), seed=n)
     B = B[:n, :n].numpy()
     dB = _cm(B)
-    assert solver.potrf(dB) == 0
+    assert any_solver.potrf(dB) == 0
     U = np.triu(_np(dB))
     Uo = oracle.potrf(B)
     assert np.abs(U - Uo).max() <= 1e-11 * np.abs(Uo).max()
@@ -55,23 +66,23 @@ def test_potrf_matches_oracle(solver, n):
     assert np.array_equal(np.tril(_np(dB), -1), np.tril(B, -1))
 
 
-def test_potrf_reports_first_bad_pivot(solver):
+def test_potrf_reports_first_bad_pivot(any_solver):
     B = inputs.make_pencil(300, seed=5)[1].numpy().copy()
     B[150, 150] = -1.0
     with pytest.raises(oracle.NotSPD) as ei:
         oracle.potrf(B)
-    assert solver.potrf(_cm(B)) == ei.value.index == 151
+    assert any_solver.potrf(_cm(B)) == ei.value.index == 151
 
 
 @pytest.mark.parametrize("n", [2, 65, 300, 777])
-def test_sygst_matches_oracle(solver, n):
+def test_sygst_matches_oracle(any_solver, n):
     A, B, _ = (t.numpy() for t in inputs.make_pencil(n, seed=10 + n))
     U = oracle.potrf(B)
     Co = oracle.sygst(A, U)
     Ain = A.copy()
     Ain[np.triu_indices(n, 1)] = 0.0  # only the lower triangle may be read
     dA = _cm(Ain)
-    solver.sygst(dA, _cm(U))
+    any_solver.sygst(dA, _cm(U))
     C = _np(dA)
     assert np.abs(C - Co).max() <= 1e-11 * np.abs(Co).max()
     assert np.array_equal(C, C.T)
@@ -90,13 +101,13 @@ def test_symv_matches_oracle(solver, n):
 
 
 @pytest.mark.parametrize("n,s", [(1, 1), (100, 1), (257, 7), (1000, 64)])
-def test_trsm_back_matches_oracle(solver, n, s):
+def test_trsm_back_matches_oracle(any_solver, n, s):
     B = inputs.make_pencil(max(n, 2), seed=3 * n)[1][:n, :n].numpy()
     U = oracle.potrf(B)
     Y = np.random.default_rng(s).standard_normal((n, s))
     Xo = oracle.backsolve(U, Y)
     dY = _cm(Y)
-    solver.trsm_back(_cm(U), dY)
+    any_solver.trsm_back(_cm(U), dY)
     X = _np(dY)
     assert np.abs(X - Xo).max() <= 1e-11 * np.abs(Xo).max()
 
@@ -127,10 +138,10 @@ def _check_pairs(A, B, w, X, w_ref, lam_all, label=""):
 
 @pytest.mark.parametrize("n,s,which", [(512, 10, "smallest"), (512, 10, "largest"), (257, 5, "smallest"),
                                        (1000, 37, "smallest"), (20, 19, "smallest"), (3, 1, "largest")])
-def test_solve_matches_oracle(solver, n, s, which):
+def test_solve_matches_oracle(any_solver, n, s, which):
     A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=n + s))
     w_or, X_or = oracle.gsyeig(A, B, s, which=which)
-    w, X, info = solver.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s, which=which)
+    w, X, info = any_solver.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s, which=which)
     w, X = _np(w), _np(X)
     assert info["nconv"] >= s
     _check_pairs(A, B, w, X, w_or, lam, f"n={n} s={s}")
@@ -139,6 +150,33 @@ def test_solve_matches_oracle(solver, n, s, which):
     cn = np.abs(lam).max()
     ang, lim = _checks.max_subspace_angle(B, X, X_or, w, lam, cn, 1e-12 * cn)
     assert ang <= lim, (ang, lim)
+
+
+def test_badly_scaled_factorisations(any_solver):
+    """Rows/columns spanning 1e-6..1e6.  Both GEMM engines must be normwise
+    backward stable (||U^T U - B|| / ||B||); the FP64 engine is also
+    column-wise accurate, which the sliced engine does not promise for such
+    inputs (its error scales with row/column maxima)."""
+    n = 700
+    A, B, _ = (t.numpy() for t in inputs.make_pencil(n, seed=21))
+    D = np.logspace(-6, 6, n)[np.random.default_rng(3).permutation(n)]
+    Bs = B * D[:, None] * D[None, :]
+    dB = _cm(Bs)
+    assert any_solver.potrf(dB) == 0
+    U = np.triu(_np(dB))
+    res = (U.T.astype(np.longdouble) @ U.astype(np.longdouble) - Bs) / np.abs(Bs).max()
+    assert float(np.abs(res).max()) <= 1e-14
+    Uo = oracle.potrf(Bs)
+    if any_solver.opts.fp64_gemm == 1:  # componentwise accuracy: FP64 engine only
+        colmax = np.abs(Uo).max(axis=0)
+        assert (np.abs(U - Uo).max(axis=0) / colmax).max() <= 1e-11
+    Y = np.random.default_rng(4).standard_normal((n, 9))
+    dY = _cm(Y)
+    any_solver.trsm_back(_cm(Uo), dY)
+    X = _np(dY)
+    # backward error of the triangular solve, normwise
+    r = (Uo.astype(np.longdouble) @ X.astype(np.longdouble) - Y)
+    assert float(np.abs(r).max()) <= 1e-13 * float(np.abs(Uo).max() * np.abs(X).max())
 
 
 def test_solve_host_pointers_match_device(solver):
@@ -226,3 +264,21 @@ def _power(M, iters=30):
         lamb = float(w.norm())
         v = w / lamb
     return lamb
+
+
+@pytest.mark.parametrize("fp64_symv,qr_restart,which", [(0, 0, "smallest"), (1, 0, "smallest"), (0, 1, "smallest"),
+                                                         (1, 1, "largest"), (0, 0, "largest")],
+                         ids=["df-thick", "fp64-thick", "df-qr", "fp64-qr-largest", "df-thick-largest"])
+def test_solve_operator_and_restart_modes(fp64_symv, qr_restart, which):
+    """Both ke1 operators (fp32 hi/lo triangle tiles, plain FP64) and both
+    restarts (thick, exact-shift implicit QR) give the oracle's eigenpairs."""
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = 777, 21
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=55))
+    w_or, X_or = oracle.gsyeig(A, B, s, which=which)
+    sol = Solver(0, fp64_symv=fp64_symv, qr_restart=qr_restart)
+    w, X, info = sol.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s, which=which)
+    assert info["restarts"] > 0
+    w, X = _np(w), _np(X)
+    _check_pairs(A, B, w, X, w_or, lam, f"fp64_symv={fp64_symv}")
