@@ -103,19 +103,20 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                : "r"(taddr));
 }
 
 // Signed 128-bit integer (h:l) times 2^e2 as a correctly rounded double
 // (round to nearest even), integer operations only.  |value| must lie in the
 // normal range (checked by the caller's exponent bounds).
-__device__ __forceinline__ double i128_ldexp(int64_t h, uint64_t l, int e2) {
-  const bool neg = h < 0;
+__device__ __forceinline__ double i128_ldexp(int64_t h, uint64_t l, int e2, bool flip) {
+  const bool neg = (h < 0) != flip;
+  const bool vneg = h < 0;
   uint64_t ah = (uint64_t)h, al = l;
-  if (neg) {  // two's complement negate
+  if (vneg) {  // two's complement negate
     al = ~al + 1;
     ah = ~ah + (al == 0 ? 1 : 0);
   }
@@ -250,20 +251,29 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
   const bool neg_alpha = alpha < 0.0;
   const int ea2 = (alpha == 0.0) ? 0 : (int)((__double_as_longlong(fabs(alpha)) >> 52) & 0x7FF) - 1023;
   const bool alpha_pow2 = (alpha != 0.0) && ((__double_as_longlong(alpha) & ((1ll << 52) - 1)) == 0);
-  for (int c0 = cgroup * (UN / 4); c0 < (cgroup + 1) * (UN / 4); c0 += 8) {
-    uint32_t v[S][8];
+  const int beta_mode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
+  for (int c0 = cgroup * (UN / 4); c0 < (cgroup + 1) * (UN / 4); c0 += 4) {
+    uint32_t v[S][4];
 #pragma unroll
-    for (int d = 0; d < S; d++) tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * UN + c0), v[d]);
+    for (int d = 0; d < S; d++) tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * UN + c0), v[d]);
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
     if (!got || gi >= M) continue;
+    // gather first (independent loads in flight together), then convert, then store
+    bool ok[4];
+    int ecv[4];
+    double cold[4];
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
+    for (int c = 0; c < 4; c++) {
       const int64_t gj = n0 + c0 + c;
-      if (gj >= N) continue;
       const int64_t dd = gi - gj + diag;
-      if (mode == TRI_LOWER && dd < 0) continue;
-      if (mode == TRI_UPPER && dd > 0) continue;
-      const int ec = eb[gj];
+      ok[c] = (gj < N) && !(mode == TRI_LOWER && dd < 0) && !(mode == TRI_UPPER && dd > 0);
+      ecv[c] = ok[c] ? eb[gj] : EXP_NONE;
+      cold[c] = (ok[c] && beta_mode != 0) ? C[gi + gj * ldc] : 0.0;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      if (!ok[c]) continue;
+      const int ec = ecv[c];
       double val = 0.0;
       if (er != EXP_NONE && ec != EXP_NONE) {
         int64_t hi = 0, lo = 0;
@@ -278,15 +288,11 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         // carry / borrow of the low-word addition
         if (lo >= 0) vh += (vl < hl) ? 1 : 0;
         else vh -= (vl > hl) ? 1 : 0;
-        if (alpha_pow2) {
-          val = i128_ldexp(vh, vl, er + ec - 64 + ea2);
-          if (neg_alpha) val = -val;
-        } else {
-          val = alpha * i128_ldexp(vh, vl, er + ec - 64);
-        }
+        if (alpha_pow2) val = i128_ldexp(vh, vl, er + ec - 64 + ea2, neg_alpha);
+        else val = alpha * i128_ldexp(vh, vl, er + ec - 64, false);
       }
-      double *pc = &C[gi + gj * ldc];
-      *pc = (beta == 0.0) ? val : (beta == 1.0 ? *pc + val : fma(beta, *pc, val));
+      const int64_t gj = n0 + c0 + c;
+      C[gi + gj * ldc] = (beta_mode == 0) ? val : (beta_mode == 1 ? cold[c] + val : fma(beta, cold[c], val));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

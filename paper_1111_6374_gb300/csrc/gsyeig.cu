@@ -271,6 +271,8 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
     h->op.W = static_cast<float2 *>(h->dfpart.p);
     const int64_t NTt = ceil_div(n, 64);
     h->op.wsplit = h->op.W + (size_t)NTt * NTt * 64;
+    h->op.err = reinterpret_cast<int *>(h->op.wsplit + (size_t)NTt * 64);
+    GS_CUDA(cudaMemsetAsync(h->op.err, 0, sizeof(int), st));
     GS_TRY(df_operator_build(st, n, C, ldc, h->op));
   }
   LanczosState *dstate = static_cast<LanczosState *>(h->state.p);
@@ -381,6 +383,12 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
   GS_CUDA(cudaEventRecord(e1, st));
   GS_CUDA(cudaEventSynchronize(e1));
   if (ms_ke3) *ms_ke3 = elapsed(e0, e1);
+  if (h->use_df) {
+    // a bounded wait inside the symv kernel that ran out invalidates the result
+    int e = 0;
+    GS_CUDA(cudaMemcpy(&e, h->op.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) return GSYEIG_TIMEOUT;
+  }
   if (info) {
     info->nconv = hs.nconv;
     info->restarts = restarts;

@@ -72,10 +72,10 @@ __global__ void k_vec_split(int64_t n, int64_t npad, const double *__restrict__ 
   }
 }
 
-// (bi, bj) of packed tile t; fp32 estimate (GB300's FP64 pipe is slow)
-// corrected by integer steps.
-__device__ __forceinline__ void tile_of(int64_t t, int64_t &bi, int64_t &bj) {
-  int64_t b = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+// (bi, bj) of packed tile t (32-bit: the tile count stays below 2^31);
+// fp32 estimate corrected by integer steps (no FP64 instruction).
+__device__ __forceinline__ void tile_of(int t, int &bi, int &bj) {
+  int b = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
   while (b * (b + 1) / 2 > t) b--;
   while ((b + 1) * (b + 2) / 2 <= t) b++;
   bi = b;
@@ -88,29 +88,84 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   return make_float2(s, a.y + b.y + q);
 }
 
-__global__ void __launch_bounds__(DF_THREADS) k_symv_df(int64_t NT, int64_t npad, const float *__restrict__ hi,
+__device__ __forceinline__ uint32_t sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// bounded mbarrier wait (false on expiry)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 24); it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(sptr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+constexpr int NSTAGE = 3;
+constexpr int TILE_BYTES = TS * TS * 4;  // one of hi / lo
+
+// Persistent CTAs; tiles t = blockIdx.x + i gridDim.x.  Thread 0 keeps
+// NSTAGE tiles in flight with cp.async.bulk (hi and lo, 16 KB each) into
+// shared memory; all 8 warps compute on the oldest one.  A wait that runs
+// out sets *err and ends the CTA after draining its own copies.
+__global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, const float *__restrict__ hi,
                                                         const float *__restrict__ lo, const float2 *__restrict__ ws,
-                                                        float2 *__restrict__ W) {
+                                                        float2 *__restrict__ W, int *err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *sh = reinterpret_cast<float *>(smem);                       // NSTAGE x (hi tile, lo tile)
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)NSTAGE * 2 * TILE_BYTES);
   __shared__ float2 xr[TS], xc[TS];  // w of the tile's column block (row sums), row block (col sums)
   __shared__ float2 rowp[4][TS];     // row-sum partials of the 4 column groups
   __shared__ float2 colp[2][TS];     // column-sum partials of the 2 row halves
+  __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = lane + 32 * (warp & 1), g = warp >> 1;  // row, column group (16 columns)
-  const int64_t ntiles = NT * (NT + 1) / 2;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int64_t bi, bj;
+  const int ntiles = NT * (NT + 1) / 2;
+  const int mine = (blockIdx.x < (unsigned)ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSTAGE; i++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sptr(&full[i])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    s_fail = 0;
+  }
+  __syncthreads();
+  auto issue = [&](int i) {  // thread 0: copies of this CTA's i-th tile into stage i % NSTAGE
+    const int t = (int)blockIdx.x + i * (int)gridDim.x;
+    const int b = i % NSTAGE;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sptr(&full[b])),
+                 "r"(2 * TILE_BYTES)
+                 : "memory");
+    const float *srcs[2] = {hi + (size_t)t * TS * TS, lo + (size_t)t * TS * TS};
+    for (int q = 0; q < 2; q++)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                       sptr(sh + (size_t)(b * 2 + q) * TS * TS)),
+                   "l"(srcs[q]), "r"(TILE_BYTES), "r"(sptr(&full[b]))
+                   : "memory");
+  };
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NSTAGE && i < mine; i++) issue(i);
+  int issued = (mine < NSTAGE) ? mine : NSTAGE;
+  for (int i = 0; i < mine; i++) {
+    const int t = (int)blockIdx.x + i * (int)gridDim.x;
+    int bi, bj;
     tile_of(t, bi, bj);
     const bool diag = (bi == bj);
-    if (threadIdx.x < TS) xr[threadIdx.x] = ws[bj * TS + threadIdx.x];
-    else if (threadIdx.x < 2 * TS) xc[threadIdx.x - TS] = ws[bi * TS + threadIdx.x - TS];
+    if (threadIdx.x < TS) xr[threadIdx.x] = ws[(int64_t)bj * TS + threadIdx.x];
+    else if (threadIdx.x < 2 * TS) xc[threadIdx.x - TS] = ws[(int64_t)bi * TS + threadIdx.x - TS];
+    const int b = i % NSTAGE;
+    const bool ok = mbar_wait(&full[b], (uint32_t)((i / NSTAGE) & 1));
+    if (!ok) s_fail = 1;
     __syncthreads();
-    const float *h = hi + t * TS * TS, *l = lo + t * TS * TS;
+    if (s_fail) break;
+    const float *h = sh + (size_t)(b * 2) * TS * TS, *l = h + TS * TS;
     float ch[16], cl[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-      const int c = g * 16 + k;
-      ch[k] = __ldg(&h[r + TS * c]);
-      cl[k] = __ldg(&l[r + TS * c]);
+      ch[k] = h[r + TS * (g * 16 + k)];
+      cl[k] = l[r + TS * (g * 16 + k)];
     }
     // row sums over this thread's 16 columns (compensated dot product)
     float rs = 0.f, rc = 0.f;
@@ -155,17 +210,27 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int64_t NT, int64_t npad
       other.y = __shfl_xor_sync(0xffffffffu, v[0].y, 1);
       if ((lane & 1) == 0) colp[warp & 1][g * 16 + (lane >> 1)] = df_add(v[0], other);
     }
-    __syncthreads();
+    __syncthreads();  // stage b fully read; partials complete
+    if (threadIdx.x == 0 && issued < mine) {
+      issue(issued);
+      issued++;
+    }
     if (threadIdx.x < TS) {
       // rows of block bi: combine the 4 column groups
       const int rr = threadIdx.x;
       float2 a = df_add(df_add(rowp[0][rr], rowp[1][rr]), df_add(rowp[2][rr], rowp[3][rr]));
-      W[bj * npad + bi * TS + rr] = a;
+      W[(int64_t)bj * npad + (int64_t)bi * TS + rr] = a;
     } else if (!diag && threadIdx.x < 2 * TS) {
       const int cc = threadIdx.x - TS;
-      W[bi * npad + bj * TS + cc] = df_add(colp[0][cc], colp[1][cc]);
+      W[(int64_t)bi * npad + (int64_t)bj * TS + cc] = df_add(colp[0][cc], colp[1][cc]);
     }
     __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // none of our bulk copies may still be landing when the CTA exits
+    for (int i = (issued > NSTAGE ? issued - NSTAGE : 0); i < issued; i++)
+      if (!mbar_wait(&full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1))) s_fail = 1;
+    if (s_fail) atomicExch(err, 1);
   }
 }
 
@@ -194,7 +259,7 @@ size_t df_operator_bytes(int64_t n) {
 
 size_t df_partials_bytes(int64_t n) {
   const int64_t NT = ceil_div(n, TS);
-  return (size_t)NT * NT * TS * sizeof(float2) + (size_t)NT * TS * sizeof(float2);
+  return (size_t)NT * NT * TS * sizeof(float2) + (size_t)NT * TS * sizeof(float2) + 256;
 }
 
 int df_operator_build(cudaStream_t st, int64_t n, const double *C, int64_t ldc, DfOperator &op) {
@@ -216,8 +281,10 @@ int df_symv(cudaStream_t st, const DfOperator &op, const double *w, double *z) {
   const int64_t ntiles = op.NT * (op.NT + 1) / 2;
   k_vec_split<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.npad, 256), 1024)), 256, 0, st>>>(
       op.n, op.npad, w, op.wsplit);
-  k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, 152 * 8), DF_THREADS, 0, st>>>(op.NT, op.npad, op.hi, op.lo,
-                                                                                 op.wsplit, op.W);
+  const size_t smem = (size_t)NSTAGE * 2 * TILE_BYTES + NSTAGE * sizeof(uint64_t);
+  GS_CUDA(cudaFuncSetAttribute((const void *)k_symv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, 152 * 2), DF_THREADS, smem, st>>>((int)op.NT, op.npad, op.hi, op.lo,
+                                                                                    op.wsplit, op.W, op.err);
   k_reduce_slots<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.n, 256), 1024)), 256, 0, st>>>(
       op.n, op.npad, op.NT, op.W, z);
   count_launch(3);

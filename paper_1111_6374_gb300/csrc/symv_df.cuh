@@ -11,10 +11,11 @@ struct DfOperator {
   float *hi = nullptr, *lo = nullptr;  // df_operator_bytes(n) starting at hi
   float2 *W = nullptr;                 // NT * npad partials
   float2 *wsplit = nullptr;            // npad split input vector
+  int *err = nullptr;                  // device flag: a bounded wait of the symv kernel expired
 };
 
 size_t df_operator_bytes(int64_t n);
-size_t df_partials_bytes(int64_t n);  // W and wsplit together
+size_t df_partials_bytes(int64_t n);  // W, wsplit and the error flag together
 // Fill op.hi/op.lo from the full symmetric C (op.hi, op.W, op.wsplit set by the caller).
 int df_operator_build(cudaStream_t st, int64_t n, const double *C, int64_t ldc, DfOperator &op);
 // z = (C_hi + C_lo) w

@@ -1,7 +1,7 @@
 // The small problems on the Lanczos tridiagonal T_m (m <= a few thousand):
-//   * eigenvalues by Sturm-count bisection (ke3; the paper's ARPACK uses a
-//     QR variant for this, Section 4.1 — bisection gives each Ritz value
-//     independently, one thread per value);
+//   * eigenvalues by Sturm-count multisection (ke3; the paper's ARPACK uses a
+//     QR variant for this, Section 4.1 -- multisection gives each Ritz value
+//     independently, one warp per value, 32 counts per round);
 //   * eigenvectors by inverse iteration (one thread per value, tridiagonal
 //     Gaussian elimination with partial pivoting), tight clusters
 //     orthogonalised afterwards;
@@ -20,8 +20,6 @@
 
 namespace gs {
 namespace {
-
-constexpr int BIS_THREADS = 128;
 
 __device__ __forceinline__ double sturm_pivmin(double maxe2) { return DBL_MIN * fmax(1.0, maxe2); }
 
@@ -52,34 +50,20 @@ __device__ int64_t sturm_below(int64_t m, int64_t ka, const double *d, const dou
   return cnt;
 }
 
-__device__ void block_minmax(double &lo, double &hi, double *sh) {
-  // sh: 2 * blockDim doubles
-  sh[threadIdx.x] = lo;
-  sh[blockDim.x + threadIdx.x] = hi;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
-      sh[blockDim.x + threadIdx.x] = fmax(sh[blockDim.x + threadIdx.x], sh[blockDim.x + threadIdx.x + s]);
-    }
-    __syncthreads();
-  }
-  lo = sh[0];
-  hi = sh[blockDim.x];
-  __syncthreads();
-}
-
-// dynamic smem: d[m], e2[m], b2[m], scratch[2*blockDim]
-__global__ void __launch_bounds__(BIS_THREADS) k_bisect(int64_t m, const double *__restrict__ d,
-                                                        const double *__restrict__ e, int64_t ka,
-                                                        const double *__restrict__ b, int64_t first, int64_t cnt,
-                                                        double *__restrict__ lam) {
+// Multisection: one warp per eigenvalue (one CTA each, spread over the
+// SMs -- GB300's FP64 pipe is narrow, so the Sturm sequences must not share
+// an SM).  Each round the 32 lanes evaluate the count at 32 interior points
+// of the bracket [a, b] and the bracket shrinks 33-fold.
+// dynamic smem: d[m], e2[m], b2[m]
+__global__ void __launch_bounds__(32) k_multisect(int64_t m, const double *__restrict__ d, const double *__restrict__ e,
+                                                  int64_t ka, const double *__restrict__ b, int64_t first,
+                                                  double *__restrict__ lam) {
   extern __shared__ double sm[];
-  double *ds = sm, *e2 = sm + m, *b2 = sm + 2 * m, *sh = sm + 3 * m;
+  double *ds = sm, *e2 = sm + m, *b2 = sm + 2 * m;
+  const int lane = threadIdx.x;
   double lo = DBL_MAX, hi = -DBL_MAX, me2 = 0.0, bsum = 0.0;
-  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+  for (int64_t i = lane; i < m; i += 32) {
     const double di = d[i];
-    // couplings of row i: arrow rows have only b_i; row ka has all b plus e[ka]; others e[i-1], e[i]
     const double el = (i > ka) ? fabs(e[i - 1]) : 0.0, er = (i >= ka && i + 1 < m) ? fabs(e[i]) : 0.0;
     const double bi = (i < ka) ? fabs(b[i]) : 0.0;
     ds[i] = di;
@@ -90,38 +74,38 @@ __global__ void __launch_bounds__(BIS_THREADS) k_bisect(int64_t m, const double 
     lo = fmin(lo, di - el - er - bi);
     hi = fmax(hi, di + el + er + bi);
   }
-  block_minmax(lo, hi, sh);
-  // row ka also carries the sum of all arrow couplings
-  __shared__ double s_bsum;
-  if (threadIdx.x == 0) s_bsum = 0.0;
-  __syncthreads();
-  atomicAdd(&s_bsum, bsum);
-  __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    me2 = fmax(me2, __shfl_xor_sync(0xffffffffu, me2, o));
+    bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+  }
   if (ka > 0) {
     const double dk = d[ka], ek = (ka + 1 < m) ? fabs(e[ka]) : 0.0;
-    lo = fmin(lo, dk - s_bsum - ek);
-    hi = fmax(hi, dk + s_bsum + ek);
+    lo = fmin(lo, dk - bsum - ek);
+    hi = fmax(hi, dk + bsum + ek);
   }
-  double tmp = -me2, dummy = 0.0;
-  block_minmax(tmp, dummy, sh);
-  me2 = -tmp;
+  __syncwarp();
   const double pivmin = sturm_pivmin(me2);
   const double span = fmax(fabs(lo), fabs(hi));
-  lo -= 2.0 * DBL_EPSILON * span + 2.0 * pivmin;
-  hi += 2.0 * DBL_EPSILON * span + 2.0 * pivmin;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  const int64_t q = first + t;  // 0-based index of the wanted eigenvalue
-  double xa = lo, xb = hi;
-  for (int it = 0; it < 256; it++) {
-    const double mid = 0.5 * (xa + xb);
-    if (xb - xa <= 2.0 * DBL_EPSILON * fmax(fabs(xa), fabs(xb)) + 4.0 * pivmin || mid == xa || mid == xb) break;
-    if (sturm_below(m, ka, ds, e2, b2, mid, pivmin) > q)
-      xb = mid;
-    else
-      xa = mid;
+  double xa = lo - 2.0 * DBL_EPSILON * span - 2.0 * pivmin;
+  double xb = hi + 2.0 * DBL_EPSILON * span + 2.0 * pivmin;
+  const int64_t q = first + blockIdx.x;  // 0-based index of the wanted eigenvalue
+  for (int it = 0; it < 64; it++) {
+    if (xb - xa <= 2.0 * DBL_EPSILON * fmax(fabs(xa), fabs(xb)) + 4.0 * pivmin) break;
+    const double step = (xb - xa) / 33.0;
+    const double x = xa + (double)(lane + 1) * step;
+    const bool le = sturm_below(m, ka, ds, e2, b2, x, pivmin) <= q;  // eigenvalue q lies above x
+    const unsigned above = __ballot_sync(0xffffffffu, !le);
+    const int L = above ? (__ffs(above) - 1) : 32;  // first lane whose point is above the eigenvalue
+    const double na = (L > 0) ? xa + (double)L * step : xa;
+    const double nb = (L < 32) ? xa + (double)(L + 1) * step : xb;
+    if (!(na < nb) || (na == xa && nb == xb)) break;
+    xa = na;
+    xb = nb;
   }
-  lam[t] = 0.5 * (xa + xb);
+  if (lane == 0) lam[blockIdx.x] = 0.5 * (xa + xb);
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -378,10 +362,10 @@ __global__ void k_converged(int64_t m, int64_t cnt, const double *theta, const d
 int tri_bisect(cudaStream_t st, int64_t m, const double *d, const double *e, int64_t ka, const double *b, int64_t first,
                int64_t cnt, double *lam) {
   if (cnt <= 0) return GSYEIG_SUCCESS;
-  size_t smem = (size_t)(3 * m + 2 * BIS_THREADS) * sizeof(double);
+  size_t smem = (size_t)(3 * m) * sizeof(double);
   if (smem > 48 * 1024)
-    GS_CUDA(cudaFuncSetAttribute((const void *)k_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_bisect<<<(unsigned)ceil_div(cnt, BIS_THREADS), BIS_THREADS, smem, st>>>(m, d, e, ka, b, first, cnt, lam);
+    GS_CUDA(cudaFuncSetAttribute((const void *)k_multisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_multisect<<<(unsigned)cnt, 32, smem, st>>>(m, d, e, ka, b, first, lam);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
@@ -391,7 +375,7 @@ int tri_invit(cudaStream_t st, int64_t m, const double *d, const double *e, int6
               const double *lam, double *Z, int64_t ldz, double *work) {
   if (cnt <= 0) return GSYEIG_SUCCESS;
   // one thread per eigenvalue, spread over many SMs (32 threads per CTA)
-  k_invit<<<(unsigned)ceil_div(cnt, 32), 32, 0, st>>>(m, d, e, ka, b, cnt, lam, Z, ldz, work);
+  k_invit<<<(unsigned)ceil_div(cnt, 8), 8, 0, st>>>(m, d, e, ka, b, cnt, lam, Z, ldz, work);
   count_launch();
   GS_CHECK_LAUNCH();
   k_cluster_orth<<<1, 256, 0, st>>>(m, cnt, lam, 0.0, d, e, Z, ldz);
