@@ -109,6 +109,17 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
                : "r"(taddr));
 }
 
+// Out-of-range tail of i128_ldexp (result subnormal or infinite): kept out of
+// line so that the compiler cannot if-convert its FP64 instructions into the
+// common path (GB300's FP64 pipe is narrow).
+__device__ __noinline__ double i128_ldexp_slow(uint64_t w, int e, bool neg) {
+  const double v = ldexp((double)w, e);
+  return neg ? -v : v;
+}
+
+// alpha * v for an alpha that is not a power of two (not used by the solver)
+__device__ __noinline__ double scale_slow(double alpha, double v) { return alpha * v; }
+
 // Signed 128-bit integer (h:l) times 2^e2 as a correctly rounded double
 // (round to nearest even), integer operations only.  |value| must lie in the
 // normal range (checked by the caller's exponent bounds).
@@ -150,7 +161,7 @@ __device__ __forceinline__ double i128_ldexp(int64_t h, uint64_t l, int e2, bool
     expo++;
   }
   const int64_t be = (int64_t)expo + 1023;
-  if (be <= 0 || be >= 2047) return neg ? -ldexp((double)w, top - 63 + e2) : ldexp((double)w, top - 63 + e2);
+  if (be <= 0 || be >= 2047) return i128_ldexp_slow(w, top - 63 + e2, neg);
   const uint64_t bits = ((uint64_t)neg << 63) | ((uint64_t)be << 52) | (mant & ((1ull << 52) - 1));
   return __longlong_as_double((long long)bits);
 }
@@ -289,7 +300,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         if (lo >= 0) vh += (vl < hl) ? 1 : 0;
         else vh -= (vl > hl) ? 1 : 0;
         if (alpha_pow2) val = i128_ldexp(vh, vl, er + ec - 64 + ea2, neg_alpha);
-        else val = alpha * i128_ldexp(vh, vl, er + ec - 64, false);
+        else val = scale_slow(alpha, i128_ldexp(vh, vl, er + ec - 64, false));
       }
       const int64_t gj = n0 + c0 + c;
       C[gi + gj * ldc] = (beta_mode == 0) ? val : (beta_mode == 1 ? cold[c] + val : fma(beta, cold[c], val));

@@ -105,7 +105,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return false;
 }
 
-constexpr int NSTAGE = 3;
+#ifndef SYMV_DF_NSTAGE
+#define SYMV_DF_NSTAGE 1
+#endif
+#ifndef SYMV_DF_CTAS_PER_SM
+#define SYMV_DF_CTAS_PER_SM 4
+#endif
+constexpr int NSTAGE = SYMV_DF_NSTAGE;        // tiles in flight per CTA
+constexpr int CTAS_PER_SM = SYMV_DF_CTAS_PER_SM;
 constexpr int TILE_BYTES = TS * TS * 4;  // one of hi / lo
 
 // Persistent CTAs; tiles t = blockIdx.x + i gridDim.x.  Thread 0 keeps
@@ -283,7 +290,7 @@ int df_symv(cudaStream_t st, const DfOperator &op, const double *w, double *z) {
       op.n, op.npad, w, op.wsplit);
   const size_t smem = (size_t)NSTAGE * 2 * TILE_BYTES + NSTAGE * sizeof(uint64_t);
   GS_CUDA(cudaFuncSetAttribute((const void *)k_symv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, 152 * 2), DF_THREADS, smem, st>>>((int)op.NT, op.npad, op.hi, op.lo,
+  k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, 152 * CTAS_PER_SM), DF_THREADS, smem, st>>>((int)op.NT, op.npad, op.hi, op.lo,
                                                                                     op.wsplit, op.W, op.err);
   k_reduce_slots<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.n, 256), 1024)), 256, 0, st>>>(
       op.n, op.npad, op.NT, op.W, z);
