@@ -131,9 +131,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    it was taken on the current source of that kernel (else None)."""
+def kernel_traffic(kernel: str, n: int):
+    """DRAM bytes per launch of `kernel` at order n, from the committed ncu
+    summary (profiles/traffic.json), if it was taken on the current source of
+    that kernel; a smaller captured case is scaled by the units it processes
+    (n^2 for the operator tiles)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -150,7 +152,9 @@ def kernel_traffic(kernel: str):
         return None
     if h != e.get("source_sha256_16"):
         return None
-    return e
+    scale = (n / e["n"]) ** 2 if e.get("scales_with") == "n^2" else 1.0
+    return {"dram_bytes": e["dram_bytes_per_launch"] * scale,
+            "note": f"ncu capture at n={e['n']} ({e['dram_bytes_per_launch']:.4g} B), scaled by {e.get('scales_with', '1')}"}
 
 
 def cpu_oracle_sample(n_full: int, s_full: int, n_sample: int):
@@ -268,28 +272,44 @@ def run_ours(args, ws, rank, local):
     if rank != 0:
         return 0
     peaks, src = load_peaks()
-    fp64_peak = peaks.get("bf16_tflops", BF16_TFLOPS) * FP64_OVER_BF16_NOMINAL
-    g_ms = sum(i["gemm_ms"] for i in infos)
-    g_fl = sum(i["gemm_flops"] for i in infos)
-    g_n = sum(i["gemm_launches"] for i in infos)
-    s_ms = sum(i["symv_ms"] for i in infos)
-    s_fl = sum(i["symv_flops"] for i in infos)
-    s_by = sum(i["symv_bytes"] for i in infos)
-    s_n = sum(i["symv_launches"] for i in infos)
-    achieved = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
-    tr = kernel_traffic("k_dgemm")
-    roof = {"kernel": "k_dgemm (FP64 GEMM engine of gs1/gs2/bt1)", "bound": "alu", "achieved": achieved,
-            "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-            "peak_source": f"{src} bf16 {peaks.get('bf16_tflops', BF16_TFLOPS)} TF/s x nominal FP64/bf16 1.25/2250 "
-                           "(GB300 FP64 FMA and FP64 mma.sync rates are equal)",
-            "traffic": (tr["dram_bytes"] if tr else None),
-            "traffic_launch": (tr["launch"] if tr else None),
-            "launches_per_step": g_n / len(infos), "ms_per_step": g_ms / len(infos),
-            "share_of_step": (g_ms / len(infos)) / ms}
-    symv = {"kernel": "k_symv_cols_v2 (ke1)", "launches_per_step": s_n / len(infos),
-            "ms_per_launch": s_ms / max(1, s_n), "achieved_gbs": s_by / (s_ms * 1e-3) / 1e9 if s_ms else 0.0,
-            "frac_hbm": (s_by / (s_ms * 1e-3) / 1e9) / peaks.get("hbm_gbs", HBM_GBS) if s_ms else 0.0,
-            "achieved_tflops": s_fl / (s_ms * 1e-3) / 1e12 if s_ms else 0.0, "share_of_step": (s_ms / len(infos)) / ms}
+    hbm = peaks.get("hbm_gbs", HBM_GBS)
+    bf16 = peaks.get("bf16_tflops", BF16_TFLOPS)
+    nst = len(infos)
+    g_ms = sum(i["gemm_ms"] for i in infos) / nst
+    g_fl = sum(i["gemm_flops"] for i in infos) / nst
+    g_n = sum(i["gemm_launches"] for i in infos) / nst
+    s_ms = sum(i["symv_ms"] for i in infos) / nst
+    s_fl = sum(i["symv_flops"] for i in infos) / nst
+    s_by = sum(i["symv_bytes"] for i in infos) / nst
+    s_n = sum(i["symv_launches"] for i in infos) / nst
+    sliced = solver.opts.fp64_gemm != 1
+    # GEMM engine of gs1/gs2/bt1: FP64-equivalent rate; on the tensor path the
+    # algorithmic tensor work is 28 bf16 digit-pair products per FP64 product
+    g_fp64eq = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+    if sliced:
+        gemm = {"kernel": "k_sliced_umma (+ slicing kernels): FP64-accurate GEMM of gs1/gs2/bt1 on tcgen05",
+                "bound": "tensor", "achieved": 28 * g_fp64eq, "peak": bf16, "unit": "TFLOP/s",
+                "frac": 28 * g_fp64eq / bf16, "fp64_equivalent_tflops": g_fp64eq,
+                "peak_source": f"{src} bf16 (MEASURED_PEAKS.json)"}
+    else:
+        fp64_peak = bf16 * FP64_OVER_BF16_NOMINAL
+        gemm = {"kernel": "k_dgemm: FP64 FMA GEMM of gs1/gs2/bt1", "bound": "alu", "achieved": g_fp64eq,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": g_fp64eq / fp64_peak,
+                "peak_source": f"{src} bf16 x nominal FP64/bf16 1.25/2250"}
+    gemm.update({"launches_per_step": g_n, "ms_per_step": g_ms, "share_of_step": g_ms / ms})
+    df = solver.opts.fp64_symv == 0
+    sym_gbs = s_by / (s_ms * 1e-3) / 1e9 if s_ms > 0 else 0.0
+    symv = {"kernel": "k_symv_df (+ split, reduce): ke1 on fp32 hi/lo triangle tiles" if df else
+            "k_symv_cols_v2: ke1 in FP64", "bound": "hbm", "achieved": sym_gbs, "peak": hbm, "unit": "GB/s",
+            "frac": sym_gbs / hbm, "peak_source": f"{src} HBM copy (MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_launch": s_by / max(1, s_n), "launches_per_step": s_n,
+            "ms_per_launch": s_ms / max(1, s_n), "fp64_equivalent_tflops": s_fl / (s_ms * 1e-3) / 1e12 if s_ms else 0.0,
+            "share_of_step": s_ms / ms}
+    for k, name in ((gemm, "k_sliced_umma" if sliced else "k_dgemm"), (symv, "k_symv_df" if df else "k_symv_cols_v2")):
+        tr = kernel_traffic(name, n)
+        k["traffic"] = tr["dram_bytes"] if tr else None
+        k["traffic_note"] = tr["note"] if tr else "no ncu capture of the current source"
+    roof = symv if symv["share_of_step"] >= gemm["share_of_step"] else gemm
     last = infos[-1]
     line = {
         "metric": METRIC, "value": ms_all / 1e3, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
@@ -303,7 +323,7 @@ def run_ours(args, ws, rank, local):
                     "ms_symv": last["symv_ms"], "ms_orth": last["orth_ms"], "ms_restart": last["restart_ms"],
                     "ms_ritz": last["ritz_ms"]},
         "accuracy": {"max_rel_eig_err_vs_constructed": rel, "max_eta": eta, "orth_err": orth},
-        "roofline": roof, "symv": symv,
+        "roofline": roof, "kernels": {"gemm": gemm, "symv": symv},
         "e2e": ({"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * s + s) * 8}
                 if e2e is not None else None),
         "gpu_launches": launches,
