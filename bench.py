@@ -10,6 +10,12 @@ vectors, back-transform) on inputs already resident in HBM; A and B are
 restored from pristine device copies between steps, outside the timed
 interval.  Inputs (2 x 2.1 GB) are far larger than the 129 MB L2.
 
+Route (--route): by default the solve takes the paper's own route for the
+smallest eigenpairs of a pencil whose A is positive definite too (Section
+3.1): the largest eigenpairs of the inverse problem B X = A X Lambda^-1.  The
+direct route (smallest eigenvalues of C = U^-T A U^-1) is timed on the same
+pencil afterwards and reported under "other_route".
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 (torchrun) runs independent replicas, one problem per GPU, no
@@ -34,6 +40,9 @@ METRIC = "time-to-solution for s gen. eigenpairs @rel. residual ≤1e-10"
 HBM_GBS = 6797.9
 BF16_TFLOPS = 1906.4
 FP64_OVER_BF16_NOMINAL = 1.25 / 2250.0  # GB300 nominal dense FP64 / bf16
+ROUTES = {"inverse": "KE on the inverse problem B X = A X Lambda^-1 (A = L^T L, largest mu = 1/lambda of "
+                     "L^-T B L^-1), as the paper does for its smallest-eigenpair workload (Section 3.1)",
+          "direct": "KE on C = U^-T A U^-1 (B = U^T U), smallest eigenvalues"}
 
 
 def load_peaks():
@@ -211,38 +220,46 @@ def run_ours(args, ws, rank, local):
     A0, B0, lam = inputs.make_pencil(n, seed=args.seed + rank, device=dev)
     A = torch.empty_like(A0)
     B = torch.empty_like(B0)
-    solver = Solver(local)
+    solver = Solver(local, inverse=1 if args.route == "inverse" else 0)
     stream = torch.cuda.current_stream(dev)
 
     def restore():
         A.copy_(A0)
         B.copy_(B0)
 
-    for _ in range(args.warmup):
-        restore()
-        w, X, info = solver.solve(A, B, s, overwrite=True)
-    torch.cuda.synchronize()
-    solver.set_options(profile=1)
-    times, infos = [], []
-    l_before = kernel_launches()
-    barrier(ws)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    def timed(sol, steps, warmup, clk=None):
+        for _ in range(warmup):
+            restore()
+            sol.solve(A, B, s, overwrite=True)
+        torch.cuda.synchronize()
+        sol.set_options(profile=1)
+        times, infos = [], []
+        for _ in range(steps):
             restore()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            w, X, info = solver.solve(A, B, s, overwrite=True)
+            w, X, info = sol.solve(A, B, s, overwrite=True)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
             infos.append(info)
+        sol.set_options(profile=0)
+        return w, X, times, infos
+
+    for _ in range(args.warmup):
+        restore()
+        w, X, info = solver.solve(A, B, s, overwrite=True)
+    torch.cuda.synchronize()
+    l_before = kernel_launches()
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        w, X, times, infos = timed(solver, args.steps, 0)
     torch.cuda.synchronize()
     barrier(ws)
     launches = (kernel_launches() - l_before) // max(1, args.steps)
-    solver.set_options(profile=0)
     ms = statistics.mean(times)
     ms_all = max_over_ranks(ms, ws, dev)
 
@@ -268,6 +285,19 @@ def run_ours(args, ws, rank, local):
             e2e_times.append(time.perf_counter() - t0)
         e2e = statistics.mean(e2e_times)
         e2e = max_over_ranks(e2e, ws, dev)
+
+    # the other route on the same pencil, for comparison (fewer steps)
+    other = None
+    if not args.no_other_route:
+        osol = Solver(local, inverse=0 if args.route == "inverse" else 1)
+        _, _, ot, oi = timed(osol, max(1, min(args.steps, 2)), 1)
+        oi = oi[-1]
+        other = {"route": "direct" if args.route == "inverse" else "inverse", "inverse_used": oi["inverse"],
+                 "ms_per_step": max_over_ranks(statistics.mean(ot), ws, dev), "steps": len(ot),
+                 "stages_ms": {k: oi[k] for k in ("ms_gs1", "ms_gs2", "ms_ke", "ms_ke3", "ms_bt1", "ms_total")},
+                 "matvecs": oi["matvecs"], "restarts": oi["restarts"], "ms_symv": oi["symv_ms"],
+                 "ms_orth": oi["orth_ms"]}
+        osol.close()
 
     if rank != 0:
         return 0
@@ -315,7 +345,8 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": ms_all / 1e3, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": n, "s": s, "which": "smallest", "krylov_dim": last["krylov_dim"],
+        "config": {"workload": args.workload, "n": n, "s": s, "which": "smallest", "route": ROUTES[args.route],
+                   "inverse_used": last["inverse"], "krylov_dim": last["krylov_dim"],
                    "keep": last["keep"], "tol": 1e-12, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (2 x %.1f GB vs 129 MB)" % (n * n * 8 / 1e9)},
         "stages_ms": {k: last[k] for k in ("ms_gs1", "ms_gs2", "ms_ke", "ms_ke3", "ms_bt1", "ms_total")},
@@ -328,6 +359,7 @@ def run_ours(args, ws, rank, local):
                 if e2e is not None else None),
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "other_route": other,
     }
     if args.gpus == 1 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(n, s, args.cpu_sample_n)
@@ -362,6 +394,10 @@ def main(argv=None):
     ap.add_argument("--cpu-sample-n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--route", choices=["inverse", "direct"], default="inverse",
+                    help="inverse: largest eigenpairs of B X = A X Lambda^-1 (A is positive definite here); "
+                         "direct: smallest of C = U^-T A U^-1")
+    ap.add_argument("--no-other-route", action="store_true", help="skip the comparison run of the other route")
     args = ap.parse_args(argv)
     args.workload = f"gsyeig n={args.n} s={args.s} smallest, FP64, known-spectrum synthetic pencil"
     ws, rank, local = dist_env()

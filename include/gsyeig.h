@@ -77,7 +77,13 @@ typedef struct {
                            the last Lanczos vector (the same subspace and projection as an exact-shift
                            implicit restart, computed in parallel); 1: implicit restart by p = m - k
                            exact-shift QR steps on T_m (Givens bulge chase), as ARPACK does */
-  int32_t reserved;     /* must be 0 */
+  int32_t inverse;      /* 0 (default): the route as stated for `which`.  1, with which = SMALLEST: when A
+                           is positive definite too, solve the inverse problem B X = A X M (M = Lambda^-1,
+                           Section 3.1) for its s LARGEST eigenvalues, which Lanczos finds in far fewer
+                           steps when the wanted lambda lie at the bottom of a wide spectrum; A is then
+                           the matrix factored and B the one transformed.  If A's Cholesky meets a
+                           non-positive pivot, A is restored and the direct route runs.  Ignored for
+                           which = LARGEST. */
 } gsyeig_opts;
 
 /* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
@@ -101,6 +107,7 @@ typedef struct {
   /* opts.profile = 1: event time of the Lanczos bookkeeping (ke2): reorthogonalisation and
    * normalisation, restarts (QR iteration on T_m and V_m Q), Ritz problems on T_m */
   double orth_ms, restart_ms, ritz_ms;
+  int64_t inverse;      /* 1 when the inverse problem (opts.inverse) was solved, else 0 */
 } gsyeig_info;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -130,6 +137,14 @@ const char *gsyeig_strerror(int status);
  *  w  (s): eigenvalues in ascending order.  Host or device pointer.
  *  dX (n x s, ldx): B-orthonormal eigenvectors, column i for w[i].
  *  info: may be NULL.
+ * With opts.inverse = 1, which = SMALLEST and A positive definite
+ * (info.inverse = 1) the roles swap: A = L^T L is factored (L written over
+ * A's upper triangle, A's strictly lower triangle kept), B is overwritten by
+ * C' = L^-T B L^-1 (full), the s largest eigenpairs (mu, y) of C' are found,
+ * and lambda = 1/mu, x = L^-1 y / sqrt(mu) are returned in the same order
+ * and normalisation (X^T B X = I) as the direct route.  B is not factored
+ * on this route: its positive definiteness is assumed, and only a wanted
+ * mu <= 0 is reported (GSYEIG_NOT_SPD with info.potrf_index = 0).
  * If dA and dB are HOST pointers the library copies them to its own device
  * workspace, leaves the host arrays unchanged, and dX must then be a host
  * pointer too (the result is copied back).  Returns GSYEIG_NOT_SPD,

@@ -49,7 +49,7 @@ struct gsyeig_ctx {
   cudaEvent_t ev[10] = {};  // 0-6 stage marks, 8 end mark, 9 user-stream ordering
   gsyeig_opts opts{};
   // workspace
-  DevBuf uinv, panel, flag;
+  DevBuf uinv, panel, flag, diag;
   DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts, arrow;
   DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
   DevBuf gemm_ws;         // slices of the tensor-core GEMM
@@ -461,7 +461,7 @@ int gsyeig_destroy(gsyeig_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
-  DevBuf *bufs[] = {&h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
+  DevBuf *bufs[] = {&h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
                     &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
                     &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
   for (DevBuf *b : bufs) b->release();
@@ -479,7 +479,7 @@ int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
   if (!(o->tol > 0.0) || o->krylov_dim < 0 || o->keep < 0 || o->max_restarts < 0 || o->timeout_ms < 0 ||
       o->block < 0 || o->block > 160 || (o->block > 0 && o->block < 16) || o->profile < 0 || o->profile > 1 ||
       o->fp64_gemm < 0 || o->fp64_gemm > 2 || o->fp64_symv < 0 || o->fp64_symv > 1 || o->qr_restart < 0 ||
-      o->qr_restart > 1 || o->reserved != 0)
+      o->qr_restart > 1 || o->inverse < 0 || o->inverse > 1)
     return -2;
   if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
   h->opts = *o;
@@ -665,27 +665,70 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   FactorWork fw;
   GS_TRY(factor_ws(h, n, nb, s, fw));
   GS_TRY(h->hw.ensure((size_t)s * sizeof(double)));
-  // gs1: B = U^T U
-  GS_CUDA(cudaEventRecord(h->ev[1], st));
-  GS_TRY(potrf_blocked(st, n, dB, dldb, nb, fw));
+  // Inverse problem (Section 3.1): with A positive definite as well, the
+  // smallest lambda of (A, B) are the largest mu = 1/lambda of (B, A), the
+  // end of C' = L^-T B L^-1 that Lanczos resolves fastest when the wanted
+  // lambda sit at the bottom of a wide spectrum.  The factored matrix F and
+  // the transformed matrix G swap roles.
+  bool inv = h->opts.inverse == 1 && which == GSYEIG_SMALLEST;
+  double *dF = dB, *dG = dA;
+  int64_t dldf = dldb, dldg = dlda;
   int flag = 0;
-  GS_CUDA(cudaMemcpyAsync(&flag, fw.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaEventRecord(h->ev[1], st));
+  if (inv) {
+    // A's lower triangle is the one read: mirror it, keep its diagonal (the
+    // only part of the lower triangle a failed Cholesky overwrites)
+    GS_TRY(symmetrize(st, n, dA, dlda, true));
+    GS_TRY(h->diag.ensure((size_t)n * sizeof(double)));
+    GS_CUDA(cudaMemcpy2DAsync(h->diag.p, sizeof(double), dA, (size_t)(dlda + 1) * sizeof(double), sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, st));
+    GS_TRY(potrf_blocked(st, n, dA, dlda, nb, fw));
+    GS_CUDA(cudaMemcpyAsync(&flag, fw.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (flag) {  // A indefinite: put its diagonal back, take the direct route
+      GS_CUDA(cudaMemcpy2DAsync(dA, (size_t)(dlda + 1) * sizeof(double), h->diag.p, sizeof(double), sizeof(double), n,
+                                cudaMemcpyDeviceToDevice, st));
+      inv = false;
+      flag = 0;
+    } else {
+      dF = dA;
+      dldf = dlda;
+      dG = dB;
+      dldg = dldb;
+      // B's upper triangle is the one read: mirror it into the lower
+      GS_TRY(symmetrize(st, n, dB, dldb, false));
+    }
+  }
+  // gs1: F = U^T U
+  if (!inv) {
+    GS_TRY(potrf_blocked(st, n, dB, dldb, nb, fw));
+    GS_CUDA(cudaMemcpyAsync(&flag, fw.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
   GS_CUDA(cudaEventRecord(h->ev[2], st));
   GS_CUDA(cudaStreamSynchronize(st));
   if (flag) {
     if (info) info->potrf_index = flag;
     return GSYEIG_NOT_SPD;
   }
-  // gs2: C = U^-T A U^-1 over A (diagonal-block inverses reused from gs1)
-  GS_TRY(sygst_blocked(st, n, dA, dlda, dB, dldb, nb, fw, true));
+  // gs2: C = U^-T G U^-1 over G (diagonal-block inverses reused from gs1)
+  GS_TRY(sygst_blocked(st, n, dG, dldg, dF, dldf, nb, fw, true));
   GS_CUDA(cudaEventRecord(h->ev[3], st));
   // ke: Lanczos on C; Ritz vectors land in X
   double ms_ke3 = 0;
-  int status = lanczos_run(h, dA, dlda, n, s, which, h->hw.d(), dX, dldx, info, &ms_ke3);
+  int status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3);
   if (status != GSYEIG_SUCCESS && status != GSYEIG_NO_CONVERGENCE && status != GSYEIG_TIMEOUT) return status;
   GS_CUDA(cudaEventRecord(h->ev[4], st));
   // bt1: X = U^-1 Y
-  GS_TRY(trsm_back_blocked(st, n, dB, dldb, dX, dldx, s, nb, fw, true));
+  GS_TRY(trsm_back_blocked(st, n, dF, dldf, dX, dldx, s, nb, fw, true));
+  if (inv) {
+    // B is assumed positive definite on this route (it is never factored);
+    // a wanted mu <= 0 shows it is not
+    double mu_min = 0.0;
+    GS_CUDA(cudaMemcpyAsync(&mu_min, h->hw.d(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (!(mu_min > 0.0)) return GSYEIG_NOT_SPD;
+    GS_TRY(lz_invert_pairs(st, n, s, h->hw.d(), dX, dldx));
+  }
   GS_CUDA(cudaMemcpyAsync(w, h->hw.p, (size_t)s * sizeof(double), cudaMemcpyDefault, st));
   if (hostA)
     GS_CUDA(cudaMemcpy2DAsync(X, ldx * sizeof(double), dX, n * sizeof(double), n * sizeof(double), s,
@@ -703,6 +746,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     info->ms_bt1 = elapsed(h->ev[4], h->ev[8]);
     info->ms_total = elapsed(h->ev[0], h->ev[8]);
     info->kernel_launches = g_launches.load() - l0;
+    info->inverse = inv ? 1 : 0;
   }
   return status;
 }

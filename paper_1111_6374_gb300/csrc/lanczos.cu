@@ -172,6 +172,28 @@ __global__ void k_zero(int64_t n, double *p) {
 
 unsigned grid1d(int64_t n, int threads) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, threads), 152 * 8)); }
 
+// Column pairs (i, s-1-i) of X swapped and scaled by 1/sqrt(mu); theta read only.
+__global__ void k_invert_cols(int64_t n, int64_t s, const double *__restrict__ theta, double *X, int64_t ldx) {
+  const int64_t half = (s + 1) / 2;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * half;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx % n, i = idx / n, k = s - 1 - i;
+    const double a = X[GS_IDX(r, i, ldx)], b = X[GS_IDX(r, k, ldx)];
+    X[GS_IDX(r, i, ldx)] = b / sqrt(theta[k]);
+    if (k != i) X[GS_IDX(r, k, ldx)] = a / sqrt(theta[i]);
+  }
+}
+
+// theta[i] <- 1 / theta[s-1-i] (one thread per pair)
+__global__ void k_invert_vals(int64_t s, double *theta) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (s + 1) / 2; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = s - 1 - i;
+    const double a = theta[i], b = theta[k];
+    theta[i] = 1.0 / b;
+    theta[k] = 1.0 / a;
+  }
+}
+
 }  // namespace
 
 int lz_nparts(int64_t n) { return (int)ceil_div(n, SUB_ROWS); }
@@ -213,6 +235,14 @@ int lz_finalize(cudaStream_t st, int64_t j, int64_t m, const double *h1, const d
                 int nparts, double *alpha, double *beta, LanczosState *state) {
   k_finalize<<<1, 256, 0, st>>>(j, m, h1, h2, sq, nparts, alpha, beta, state);
   count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int lz_invert_pairs(cudaStream_t st, int64_t n, int64_t s, double *theta, double *X, int64_t ldx) {
+  k_invert_cols<<<grid1d(n * ((s + 1) / 2), 256), 256, 0, st>>>(n, s, theta, X, ldx);
+  k_invert_vals<<<1, 128, 0, st>>>(s, theta);
+  count_launch(2);
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
 }

@@ -34,6 +34,10 @@ int lz_random(cudaStream_t st, int64_t n, uint64_t seed, uint64_t stream, double
 // and e[i] = 0 for i < k (S is m x k, ld m).
 int lz_thick_restart(cudaStream_t st, int64_t m, int64_t k, const double *theta, const double *S, double *d, double *e,
                      double *b);
+// Inverse problem (B x = mu A x, theta = its s largest mu, ascending) back to
+// (A, B): X column i <- X column s-1-i / sqrt(theta[s-1-i]) and
+// theta[i] <- 1 / theta[s-1-i], so lambda ascends and X^T B X = I.
+int lz_invert_pairs(cudaStream_t st, int64_t n, int64_t s, double *theta, double *X, int64_t ldx);
 int lz_restart_residual(cudaStream_t st, int64_t n, int64_t k, int64_t m, const double *Vq, int64_t ldvq,
                         const double *vm, const double *betaP, const double *beta, const double *Q, int64_t ldq,
                         double *f);

@@ -152,6 +152,48 @@ def test_solve_matches_oracle(any_solver, n, s, which):
     assert ang <= lim, (ang, lim)
 
 
+@pytest.mark.parametrize("n,s", [(512, 10), (1000, 37), (300, 1), (129, 64)])
+def test_solve_inverse_problem_matches_oracle(n, s):
+    """opts.inverse = 1 (Section 3.1: the largest eigenpairs of the inverse
+    problem B X = A X Lambda^-1, A positive definite) returns the oracle's s
+    smallest pairs of (A, B), ascending and B-orthonormal, in fewer Lanczos
+    steps than the direct route on this spectrum."""
+    from paper_1111_6374_gb300 import Solver
+
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=n + s + 1))
+    assert lam.min() > 0  # A = U^T Q diag(lam) Q^T U is positive definite
+    w_or, X_or = oracle.gsyeig(A, B, s)
+    w, X, info = Solver(0, inverse=1).solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s)
+    assert info["inverse"] == 1 and info["nconv"] >= s
+    w, X = _np(w), _np(X)
+    _check_pairs(A, B, w, X, w_or, lam, f"inverse n={n} s={s}")
+    assert np.max(np.abs(w - lam[:s]) / lam[:s]) <= 1e-10
+    cn = np.abs(lam).max()
+    ang, lim = _checks.max_subspace_angle(B, X, X_or, w, lam, cn, 1e-12 * cn)
+    assert ang <= lim, (ang, lim)
+    _, _, info_d = Solver(0).solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s)
+    assert info_d["inverse"] == 0
+    if n >= 512:
+        assert info["matvecs"] < info_d["matvecs"], (info["matvecs"], info_d["matvecs"])
+
+
+def test_solve_inverse_falls_back_to_direct_route():
+    """opts.inverse = 1 with an indefinite A: the Cholesky of A fails, A is
+    restored and the direct route returns the oracle's pairs; with
+    which = largest the option is ignored."""
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = 400, 9
+    lam = np.sort(np.random.default_rng(8).uniform(-500.0, 500.0, n))
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=8, lam=lam))
+    sol = Solver(0, inverse=1)
+    for which in ("smallest", "largest"):
+        w_or, X_or = oracle.gsyeig(A, B, s, which=which)
+        w, X, info = sol.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s, which=which)
+        assert info["inverse"] == 0
+        _check_pairs(A, B, _np(w), _np(X), w_or, lam, f"fallback {which}")
+
+
 def test_badly_scaled_factorisations(any_solver):
     """Rows/columns spanning 1e-6..1e6.  Both GEMM engines must be normwise
     backward stable (||U^T U - B|| / ||B||); the FP64 engine is also
