@@ -125,25 +125,44 @@ int trtri_diag_blocks(cudaStream_t st, int64_t n, const double *U, int64_t ldu, 
   return GSYEIG_SUCCESS;
 }
 
+// Two-level blocking: inner steps of nb (the diagonal-block kernels and the
+// panels) and outer blocks of NB = kOuter nb.  Within an outer block the
+// inner rank-nb updates touch only the rest of the outer block; the trailing
+// matrix beyond it receives one rank-NB update per outer block, so the
+// GEMM engine's per-element epilogue is paid once per NB columns of K
+// instead of once per nb.
+constexpr int kOuter = 4;
+
 int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, FactorWork &w) {
   size_t sm = diag_smem_bytes(nb);
   GS_TRY(set_smem((const void *)k_potrf_diag, sm));
   GS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
-  for (int64_t k0 = 0; k0 < n; k0 += nb) {
-    const int kb = (int)std::min<int64_t>(nb, n - k0);
-    double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
-    k_potrf_diag<<<1, DIAG_THREADS, sm, st>>>(B, ldb, k0, kb, nb, Uinv_k, w.flag);
-    count_launch();
-    GS_CHECK_LAUNCH();
-    const int64_t rest = n - k0 - kb;
-    if (rest <= 0) break;
-    double *Bk = &B[GS_IDX(k0, k0 + kb, ldb)];
-    // U_k,rest = U_kk^-T B_k,rest  (panel, kb x rest, staged)
-    GS_TRY(dgemm(st, true, false, kb, rest, kb, 1.0, Uinv_k, nb, Bk, ldb, 0.0, w.panel, kb, TRI_ALL, 0, w.flag));
-    GS_TRY(copy_block(st, kb, rest, w.panel, kb, Bk, ldb, w.flag));
-    // B_rest,rest (upper) -= U_k,rest^T U_k,rest
-    double *Bt = &B[GS_IDX(k0 + kb, k0 + kb, ldb)];
-    GS_TRY(dgemm(st, true, false, rest, rest, kb, -1.0, w.panel, kb, w.panel, kb, 1.0, Bt, ldb, TRI_UPPER, 0, w.flag));
+  const int64_t NB = (int64_t)kOuter * nb;
+  for (int64_t J0 = 0; J0 < n; J0 += NB) {
+    const int64_t J1 = std::min(n, J0 + NB);
+    for (int64_t k0 = J0; k0 < J1; k0 += nb) {
+      const int kb = (int)std::min<int64_t>(nb, J1 - k0);
+      double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
+      k_potrf_diag<<<1, DIAG_THREADS, sm, st>>>(B, ldb, k0, kb, nb, Uinv_k, w.flag);
+      count_launch();
+      GS_CHECK_LAUNCH();
+      const int64_t rest = n - k0 - kb;
+      if (rest <= 0) break;
+      double *Bk = &B[GS_IDX(k0, k0 + kb, ldb)];
+      // U_k,rest = U_kk^-T B_k,rest  (panel, kb x rest, staged)
+      GS_TRY(dgemm(st, true, false, kb, rest, kb, 1.0, Uinv_k, nb, Bk, ldb, 0.0, w.panel, kb, TRI_ALL, 0, w.flag));
+      GS_TRY(copy_block(st, kb, rest, w.panel, kb, Bk, ldb, w.flag));
+      // rows of the outer block below this step: B (upper) -= U_k,.^T U_k,.
+      const int64_t rin = J1 - k0 - kb;
+      if (rin > 0)
+        GS_TRY(dgemm(st, true, false, rin, rest, kb, -1.0, w.panel, kb, w.panel, kb, 1.0,
+                     &B[GS_IDX(k0 + kb, k0 + kb, ldb)], ldb, TRI_UPPER, 0, w.flag));
+    }
+    // trailing matrix beyond the outer block (upper) -= U_J,rest^T U_J,rest
+    const int64_t r2 = n - J1;
+    if (r2 > 0)
+      GS_TRY(dgemm(st, true, false, r2, r2, J1 - J0, -1.0, &B[GS_IDX(J0, J1, ldb)], ldb, &B[GS_IDX(J0, J1, ldb)], ldb,
+                   1.0, &B[GS_IDX(J1, J1, ldb)], ldb, TRI_UPPER, 0, w.flag));
   }
   return GSYEIG_SUCCESS;
 }
@@ -152,30 +171,46 @@ int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const doub
                   FactorWork &w, bool have_uinv) {
   GS_TRY(symmetrize(st, n, A, lda, true));
   if (!have_uinv) GS_TRY(trtri_diag_blocks(st, n, U, ldu, nb, w.Uinv));
+  const int64_t NB = (int64_t)kOuter * nb;
   // Step 1: W = U^-T A, block row by block row (forward substitution).
-  for (int64_t k0 = 0; k0 < n; k0 += nb) {
-    const int kb = (int)std::min<int64_t>(nb, n - k0);
-    const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
-    double *Ak = &A[GS_IDX(k0, 0, lda)];
-    GS_TRY(dgemm(st, true, false, kb, n, kb, 1.0, Uinv_k, nb, Ak, lda, 0.0, w.panel, kb));
-    GS_TRY(copy_block(st, kb, n, w.panel, kb, Ak, lda));
-    const int64_t rest = n - k0 - kb;
-    if (rest > 0)
-      GS_TRY(dgemm(st, true, false, rest, n, kb, -1.0, &U[GS_IDX(k0, k0 + kb, ldu)], ldu, w.panel, kb, 1.0,
-                   &A[GS_IDX(k0 + kb, 0, lda)], lda));
+  for (int64_t J0 = 0; J0 < n; J0 += NB) {
+    const int64_t J1 = std::min(n, J0 + NB);
+    for (int64_t k0 = J0; k0 < J1; k0 += nb) {
+      const int kb = (int)std::min<int64_t>(nb, J1 - k0);
+      const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
+      double *Ak = &A[GS_IDX(k0, 0, lda)];
+      GS_TRY(dgemm(st, true, false, kb, n, kb, 1.0, Uinv_k, nb, Ak, lda, 0.0, w.panel, kb));
+      GS_TRY(copy_block(st, kb, n, w.panel, kb, Ak, lda));
+      const int64_t rin = J1 - k0 - kb;  // rows of the outer block below this step
+      if (rin > 0)
+        GS_TRY(dgemm(st, true, false, rin, n, kb, -1.0, &U[GS_IDX(k0, k0 + kb, ldu)], ldu, w.panel, kb, 1.0,
+                     &A[GS_IDX(k0 + kb, 0, lda)], lda));
+    }
+    const int64_t r2 = n - J1;  // rows beyond the outer block: one rank-NB update
+    if (r2 > 0)
+      GS_TRY(dgemm(st, true, false, r2, n, J1 - J0, -1.0, &U[GS_IDX(J0, J1, ldu)], ldu, &A[GS_IDX(J0, 0, lda)], lda,
+                   1.0, &A[GS_IDX(J1, 0, lda)], lda));
   }
   // Step 2: lower triangle of C = W U^-1, block column by block column.
-  for (int64_t k0 = 0; k0 < n; k0 += nb) {
-    const int kb = (int)std::min<int64_t>(nb, n - k0);
-    const int64_t rows = n - k0;
-    const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
-    double *Ck = &A[GS_IDX(k0, k0, lda)];
-    GS_TRY(dgemm(st, false, false, rows, kb, kb, 1.0, Ck, lda, Uinv_k, nb, 0.0, w.panel, rows));
-    GS_TRY(copy_block(st, rows, kb, w.panel, rows, Ck, lda));
-    const int64_t rest = n - k0 - kb;
-    if (rest > 0)
-      GS_TRY(dgemm(st, false, false, rest, rest, kb, -1.0, &w.panel[kb], rows, &U[GS_IDX(k0, k0 + kb, ldu)], ldu,
-                   1.0, &A[GS_IDX(k0 + kb, k0 + kb, lda)], lda, TRI_LOWER, 0));
+  for (int64_t J0 = 0; J0 < n; J0 += NB) {
+    const int64_t J1 = std::min(n, J0 + NB);
+    for (int64_t k0 = J0; k0 < J1; k0 += nb) {
+      const int kb = (int)std::min<int64_t>(nb, J1 - k0);
+      const int64_t rows = n - k0;
+      const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
+      double *Ck = &A[GS_IDX(k0, k0, lda)];
+      GS_TRY(dgemm(st, false, false, rows, kb, kb, 1.0, Ck, lda, Uinv_k, nb, 0.0, w.panel, rows));
+      GS_TRY(copy_block(st, rows, kb, w.panel, rows, Ck, lda));
+      const int64_t rest = n - k0 - kb;
+      const int64_t cin = J1 - k0 - kb;  // columns of the outer block right of this step
+      if (cin > 0)
+        GS_TRY(dgemm(st, false, false, rest, cin, kb, -1.0, &w.panel[kb], rows, &U[GS_IDX(k0, k0 + kb, ldu)], ldu,
+                     1.0, &A[GS_IDX(k0 + kb, k0 + kb, lda)], lda, TRI_LOWER, 0));
+    }
+    const int64_t r2 = n - J1;  // lower trailing matrix beyond the outer block: one rank-NB update
+    if (r2 > 0)
+      GS_TRY(dgemm(st, false, false, r2, r2, J1 - J0, -1.0, &A[GS_IDX(J1, J0, lda)], lda, &U[GS_IDX(J0, J1, ldu)],
+                   ldu, 1.0, &A[GS_IDX(J1, J1, lda)], lda, TRI_LOWER, 0));
   }
   GS_TRY(symmetrize(st, n, A, lda, true));
   return GSYEIG_SUCCESS;

@@ -219,13 +219,31 @@ int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64
   KernelProfiler *prof = current_profiler();
   size_t e0 = prof ? prof->start(st) : SIZE_MAX;
   GemmContext *gc = current_gemm();
-  if (gc && gc->sliced && gc->umma && K >= 1 && K <= 128 && gc->ws_bytes >= umma_workspace_bytes(M, N, K)) {
-    GS_TRY(umma_gemm(st, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, mode, diag, abort_flag,
-                     gc->ws, gc->ws_bytes, gc->err));
-  } else if (gc && gc->sliced && !gc->umma && K >= 1 && K <= 128 && gc->ws_bytes >= sliced_workspace_bytes(M, N, K)) {
-    GS_TRY(sliced_gemm(st, transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, mode, diag, abort_flag,
-                       gc->ws, gc->ws_bytes));
-  } else {
+  // the sliced engines take K in slabs (tcgen05: up to 512, exact chunks of
+  // 128 inside; mma.sync: 128), C accumulating from the second slab on
+  const int64_t kslab = (gc && gc->sliced) ? (gc->umma ? 512 : 128) : K;
+  bool done = false;
+  if (gc && gc->sliced && K >= 1) {
+    const int64_t kc0 = std::min(K, kslab);
+    const bool ws_ok = gc->umma ? gc->ws_bytes >= umma_workspace_bytes(M, N, kc0)
+                                : gc->ws_bytes >= sliced_workspace_bytes(M, N, kc0);
+    if (ws_ok) {
+      for (int64_t k0 = 0; k0 < K; k0 += kslab) {
+        const int64_t kc = std::min(kslab, K - k0);
+        const double *Ak = transA ? A + k0 : A + k0 * lda;  // op(A) is M x K
+        const double *Bk = transB ? B + k0 * ldb : B + k0;  // op(B) is K x N
+        const double bk = (k0 == 0) ? beta : 1.0;
+        if (gc->umma)
+          GS_TRY(umma_gemm(st, transA, transB, M, N, kc, alpha, Ak, lda, Bk, ldb, bk, C, ldc, mode, diag, abort_flag,
+                           gc->ws, gc->ws_bytes, gc->err));
+        else
+          GS_TRY(sliced_gemm(st, transA, transB, M, N, kc, alpha, Ak, lda, Bk, ldb, bk, C, ldc, mode, diag, abort_flag,
+                             gc->ws, gc->ws_bytes));
+      }
+      done = true;
+    }
+  }
+  if (!done) {
     dim3 grid((unsigned)ceil_div(M, BM), (unsigned)ceil_div(N, BN));
     k_dgemm<<<grid, NT, 0, st>>>(transA, transB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, (int)mode, diag,
                                  abort_flag);

@@ -10,15 +10,20 @@
 //    (56 KB) or a 64-row B block (28 KB) is one contiguous run: each stage is
 //    brought in by a single cp.async.bulk per operand, completing on an
 //    mbarrier (no tensor map needed).
-//  * One thread issues tcgen05.mma.kind::f16 (bf16 x bf16 -> fp32, M = 128,
-//    N = 64, K = 16); the accumulator of level d lives in TMEM columns
-//    [64 d, 64 d + 64) (7 levels, 448 columns, 512 allocated).  Each K stage
-//    is 2 x 28 MMAs; tcgen05.commit releases the stage buffer.
-//  * Epilogue (16 warps; warp w reads TMEM lane quarter w % 4, a quarter of
-//    the columns each): tcgen05.ld of the 7 level sums of a row, exact
-//    recombination in 128-bit integers and a
+//  * Persistent CTAs (one per SM) walk the 128 x 64 tiles of C with
+//    warp-specialised roles: a producer lane, an MMA lane and 16 epilogue
+//    warps.  One thread issues tcgen05.mma.kind::f16 (bf16 x bf16 -> fp32,
+//    M = 128, N = 64, K = 16); the accumulator of level d lives in TMEM
+//    columns [64 d, 64 d + 64) (7 levels, 448 columns, 512 allocated).  Each
+//    K stage is 2 x 28 MMAs; tcgen05.commit releases the stage buffer.
+//  * K up to 512 per call, in exact chunks of K = 128: after each chunk the
+//    epilogue (warp w reads TMEM lane quarter w % 4, a quarter of the
+//    columns each) reads the 7 level sums with tcgen05.ld, recombines them
+//    exactly into a 128-bit integer per element added to a register
+//    accumulator, and hands TMEM back to the next chunk's MMAs; after the
+//    last chunk C += V 2^e is added and rounded in integer arithmetic (a
 //    correctly rounded integer-only conversion to FP64 with the row/column
-//    exponents folded in; the FP64 pipe only does the final C update.
+//    exponents folded in): GB300's narrow FP64 pipe is not used.
 //  * Every mbarrier wait is bounded; on expiry the kernel records the fault
 //    in *err, still waits (bounded) for its own copies, frees its TMEM and
 //    returns.
@@ -37,9 +42,17 @@ constexpr int B_K16_BYTES = UN * 16 * 2;     // 2048
 constexpr int A_STAGE = S * 2 * A_K16_BYTES; // 57344
 constexpr int B_STAGE = S * 2 * B_K16_BYTES; // 28672
 constexpr int NBUF = 2;
-constexpr int UMMA_THREADS = 512;  // 16 warps: the epilogue splits each TMEM lane quarter over 4 warps
+constexpr int CH_STAGES = 128 / UKS;  // K stages per exact chunk (level sums exact for K <= 128)
+constexpr int UMMA_MAX_K = 512;
 constexpr int TMEM_COLS = 512;
 constexpr uint32_t SPIN_LIMIT = 1u << 24;
+
+int num_sms() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
 
 // ---------------------------------------------------------------- PTX -----
 __device__ __forceinline__ uint32_t sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -132,26 +145,23 @@ __device__ __forceinline__ double i128_ldexp(int64_t h, uint64_t l, int e2, bool
     ah = ~ah + (al == 0 ? 1 : 0);
   }
   if (ah == 0 && al == 0) return 0.0;
-  int lz = ah ? __clzll((long long)ah) : 64 + __clzll((long long)al);
+  const int lz = ah ? __clzll((long long)ah) : 64 + __clzll((long long)al);
   const int top = 127 - lz;  // index of the leading bit
-  // bring the leading bit to position 63 of a 64-bit word, keep a sticky bit
+  // shift the 128-bit magnitude left by lz: bit `top` lands at bit 127;
+  // w = bits [top, top - 63], rest = everything below (sticky)
   uint64_t w, rest;
-  const int s = 63 - top;  // left shift of the 128-bit value so that bit `top` lands at 127
-  const int shl = lz;      // same thing for the 128-bit word
-  if (shl == 0) {
+  if (lz == 0) {
     w = ah;
     rest = al;
-  } else if (shl < 64) {
-    w = (ah << shl) | (al >> (64 - shl));
-    rest = al << shl;
+  } else if (lz < 64) {
+    w = (ah << lz) | (al >> (64 - lz));
+    rest = al << lz;
   } else {
-    w = al << (shl - 64);
+    w = al << (lz - 64);
     rest = 0;
   }
-  (void)s;
-  // w holds bits [top, top-63]; mantissa = top 53 bits of w
-  uint64_t mant = w >> 11;
-  const uint64_t rbits = w & 0x7FF;  // 11 dropped bits of w
+  uint64_t mant = w >> 11;  // top 53 bits
+  const uint64_t rbits = w & 0x7FF;
   const bool half = (rbits & 0x400) != 0;
   const bool sticky = ((rbits & 0x3FF) != 0) || (rest != 0);
   if (half && (sticky || (mant & 1))) mant++;
@@ -166,31 +176,139 @@ __device__ __forceinline__ double i128_ldexp(int64_t h, uint64_t l, int e2, bool
   return __longlong_as_double((long long)bits);
 }
 
+// Out-of-line FP64 form of c + (-1)^flip V 2^e2 for the cases the integer
+// path below does not take (c subnormal, infinite or NaN, or c far below the
+// product's last bit).
+__device__ __noinline__ double add_slow(double c, int64_t h, uint64_t l, int e2, bool flip) {
+  return c + i128_ldexp(h, l, e2, flip);
+}
+
+// c + (-1)^flip V 2^e2 (V = h:l, |V| < 2^73) correctly rounded, in integer
+// arithmetic: both terms are aligned on the lower of their last-bit
+// exponents and added exactly in 128 bits, then rounded once.  With c's
+// last bit at 2^ec (c = +-mc 2^ec, mc < 2^53) and sh = ec - e2:
+//   sh > 72:        |V 2^e2| < 2^(e2+73) <= ulp(c)/2, the sum rounds to c;
+//   0 <= sh <= 72:  c 2^-e2 = mc 2^sh < 2^125, the sum fits in 127 bits;
+//   -54 <= sh < 0:  V 2^-sh < 2^127, the sum fits with its last bit at 2^ec;
+//   sh < -54:       the FP64 path.
+__device__ __forceinline__ double add_i128(double c, int64_t h, uint64_t l, int e2, bool flip) {
+  if (h == 0 && l == 0) return c;
+  const uint64_t cb = (uint64_t)__double_as_longlong(c);
+  const int ce = (int)((cb >> 52) & 0x7FF);
+  if ((cb << 1) == 0) return i128_ldexp(h, l, e2, flip);  // c = +-0
+  if (ce == 0 || ce == 0x7FF) return add_slow(c, h, l, e2, flip);
+  const int sh = (ce - 1075) - e2;
+  if (sh > 72) return c;
+  if (sh < -54) return add_slow(c, h, l, e2, flip);
+  if (flip) {  // V <- -V
+    l = ~l + 1;
+    h = (int64_t)(~(uint64_t)h + (l == 0 ? 1 : 0));
+  }
+  const uint64_t mc = (cb & ((1ull << 52) - 1)) | (1ull << 52);
+  uint64_t th, tl;  // aligned magnitude of c
+  uint64_t vh = (uint64_t)h, vl = l;
+  int e;
+  if (sh >= 0) {
+    tl = (sh < 64) ? (mc << sh) : 0;
+    th = (sh == 0) ? 0 : (sh < 64 ? (mc >> (64 - sh)) : (mc << (sh - 64)));
+    e = e2;
+  } else {
+    const int k = -sh;  // shift V left by k (1..54)
+    vh = (vh << k) | (vl >> (64 - k));
+    vl <<= k;
+    tl = mc;
+    th = 0;
+    e = ce - 1075;
+  }
+  if (cb >> 63) {  // subtract |c|
+    const uint64_t nl = vl - tl;
+    vh = vh - th - (vl < tl ? 1 : 0);
+    vl = nl;
+  } else {
+    const uint64_t nl = vl + tl;
+    vh = vh + th + (nl < vl ? 1 : 0);
+    vl = nl;
+  }
+  return i128_ldexp((int64_t)vh, vl, e, false);
+}
+
+// Persistent CTAs, one per SM; tile t = blockIdx.x + i gridDim.x over the
+// (M / 128) x (N / 64) grid of C (column-major in m), tiles outside the
+// triangle of a TRI mode skipped by every role alike.
+//   warp 16 (one lane): producer -- bulk copies of each K stage into a
+//       2-deep ring, released by the MMA commits;
+//   warp 17 (one lane): MMA issuer -- waits for the epilogue to have drained
+//       the accumulators of the previous tile, then 28 x 2 MMAs per stage;
+//   warps 0-15: epilogue -- read the 7 level sums of 16 elements each from
+//       TMEM, fold them into 128-bit integers in registers, hand TMEM back
+//       (the next tile's MMAs start), then update C from the registers.
+// Every wait is bounded; a wait that runs out sets s_fail, every role leaves
+// its loop, the MMA issuer waits (bounded) for its own MMAs and thread 0 for
+// the producer's copies before TMEM is freed.
+constexpr int EPI_WARPS = 16;
+constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
+constexpr int UMMA_THREADS = (EPI_WARPS + 2) * 32;
+constexpr int EPI_COLS = UN / (EPI_WARPS / 4);  // columns of a tile per epilogue warp (16)
+
+// Exact integer value of a level sum (an integer-valued fp32, |x| < 2^24).
+__device__ __forceinline__ int32_t lvl(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
+
+// (vh:vl) += V for the 7 level sums v[0..6] of one element,
+// V = sum_d L_d 256^(6-d), |L_d| <= (d + 1) 128 2^14 (K <= 128 per chunk):
+// a = L0 256 + L1 and b = L2 256 + L3 fit in int32, P = a 2^16 + b < 2^47,
+// Q = (L4 256 + L5) 256 + L6 < 2^41, V = P 2^24 + Q.
+__device__ __forceinline__ void fold_add(const uint32_t (&v)[S], int32_t &vh, uint64_t &vl) {
+  const int32_t a = lvl(v[0]) * 256 + lvl(v[1]);
+  const int32_t b = lvl(v[2]) * 256 + lvl(v[3]);
+  const int64_t P = (int64_t)a * 65536 + (int64_t)b;
+  const int64_t Q = ((int64_t)lvl(v[4]) * 256 + (int64_t)lvl(v[5])) * 256 + (int64_t)lvl(v[6]);
+  const uint64_t pl = (uint64_t)P << 24;
+  const uint64_t l1 = pl + (uint64_t)Q;
+  int32_t h = (int32_t)(P >> 40) + (int32_t)(Q >> 63) + (l1 < pl ? 1 : 0);
+  const uint64_t l2 = vl + l1;
+  vh += h + (l2 < vl ? 1 : 0);
+  vl = l2;
+}
+
+struct TileGrid {
+  int64_t M, N, diag;
+  int mt, nt, mode;
+  __device__ bool get(int t, int64_t &m0, int64_t &n0) const {
+    m0 = (int64_t)(t % mt) * UM;
+    n0 = (int64_t)(t / mt) * UN;
+    if (mode == TRI_LOWER && (m0 + UM - 1) - n0 + diag < 0) return false;
+    if (mode == TRI_UPPER && m0 - (n0 + UN - 1) + diag > 0) return false;
+    return true;
+  }
+};
+
+__device__ __forceinline__ bool failed(const int *f) { return *(volatile const int *)f != 0; }
+
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
-    k_sliced_umma(int64_t M, int64_t N, int64_t nks, const unsigned char *__restrict__ SA,
-                  const unsigned char *__restrict__ SB, const int *__restrict__ ea, const int *__restrict__ eb,
-                  double alpha, double beta, double *__restrict__ C, int64_t ldc, int mode, int64_t diag,
-                  const int *abort_flag, int *err) {
+    k_sliced_umma(TileGrid g, int64_t nks, const unsigned char *__restrict__ SA, const unsigned char *__restrict__ SB,
+                  const int *__restrict__ ea, const int *__restrict__ eb, double alpha, double beta,
+                  double *__restrict__ C, int64_t ldc, const int *abort_flag, int *err) {
   if (abort_flag && *abort_flag) return;
-  const int64_t m0 = (int64_t)blockIdx.x * UM, n0 = (int64_t)blockIdx.y * UN;
-  if (mode == TRI_LOWER && (m0 + UM - 1) - n0 + diag < 0) return;
-  if (mode == TRI_UPPER && m0 - (n0 + UN - 1) + diag > 0) return;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char *bufA = smem;                             // NBUF x A_STAGE
-  unsigned char *bufB = smem + NBUF * A_STAGE;            // NBUF x B_STAGE
+  unsigned char *bufA = smem;                   // NBUF x A_STAGE
+  unsigned char *bufB = smem + NBUF * A_STAGE;  // NBUF x B_STAGE
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NBUF * (A_STAGE + B_STAGE));
-  uint64_t *full = bars, *empty = bars + NBUF, *accb = bars + 2 * NBUF;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NBUF + 1);
+  uint64_t *full = bars, *empty = bars + NBUF, *acc_full = bars + 2 * NBUF, *acc_empty = acc_full + 1,
+           *fin = acc_full + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NBUF + 3);
   __shared__ int s_fail;
-  __shared__ int s_issued;  // stages whose bulk copies were issued
+  __shared__ int64_t s_issued;  // stages whose bulk copies were issued
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntile = g.mt * g.nt;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NBUF; i++) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    mbar_init(accb, 1);
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, EPI_WARPS);
+    mbar_init(fin, 1);
     s_fail = 0;
     s_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -204,116 +322,184 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const unsigned char *gA = SA + (size_t)blockIdx.x * nks * A_STAGE;
-  const unsigned char *gB = SB + (size_t)blockIdx.y * nks * B_STAGE;
 
-  if (warp == 0 && lane == 0) {
-    // producer: one bulk copy per operand per stage
-    for (int64_t ks = 0; ks < nks; ks++) {
-      const int b = (int)(ks % NBUF);
-      if (ks >= NBUF && !mbar_wait(&empty[b], (uint32_t)(((ks / NBUF) - 1) & 1))) {
-        atomicExch(&s_fail, 1);
-        break;
+  if (warp == PRODUCER_WARP) {
+    if (lane == 0) {
+      int64_t it = 0;
+      for (int t = blockIdx.x; t < ntile && !failed(&s_fail); t += gridDim.x) {
+        int64_t m0, n0;
+        if (!g.get(t, m0, n0)) continue;
+        const unsigned char *gA = SA + (size_t)(m0 / UM) * nks * A_STAGE;
+        const unsigned char *gB = SB + (size_t)(n0 / UN) * nks * B_STAGE;
+        for (int64_t ks = 0; ks < nks; ks++, it++) {
+          const int b = (int)(it % NBUF);
+          if (it >= NBUF && !mbar_wait(&empty[b], (uint32_t)(((it / NBUF) - 1) & 1))) {
+            atomicExch(&s_fail, 1);
+            break;
+          }
+          if (failed(&s_fail)) break;
+          mbar_expect_tx(&full[b], A_STAGE + B_STAGE);
+          bulk_g2s(bufA + (size_t)b * A_STAGE, gA + (size_t)ks * A_STAGE, A_STAGE, &full[b]);
+          bulk_g2s(bufB + (size_t)b * B_STAGE, gB + (size_t)ks * B_STAGE, B_STAGE, &full[b]);
+          s_issued = it + 1;
+        }
       }
-      mbar_expect_tx(&full[b], A_STAGE + B_STAGE);
-      bulk_g2s(bufA + (size_t)b * A_STAGE, gA + (size_t)ks * A_STAGE, A_STAGE, &full[b]);
-      bulk_g2s(bufB + (size_t)b * B_STAGE, gB + (size_t)ks * B_STAGE, B_STAGE, &full[b]);
-      s_issued = (int)ks + 1;
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    const uint32_t idesc = instr_desc();
-    bool ok = true;
-    for (int64_t ks = 0; ks < nks && ok; ks++) {
-      const int b = (int)(ks % NBUF);
-      if (!mbar_wait(&full[b], (uint32_t)((ks / NBUF) & 1))) {
-        atomicExch(&s_fail, 1);
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t a0 = sptr(bufA + (size_t)b * A_STAGE), b0 = sptr(bufB + (size_t)b * B_STAGE);
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc();
+      int64_t it = 0;
+      int64_t fc = 0;  // chunks handed to the epilogue
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+        int64_t m0, n0;
+        if (!g.get(t, m0, n0)) continue;
+        for (int64_t ks = 0; ks < nks; ks++, it++) {
+          const int b = (int)(it % NBUF);
+          const bool first = (ks % CH_STAGES) == 0;  // first stage of an exact K chunk
+          if (first) {
+            // the epilogue has folded the previous chunk's accumulators out of TMEM
+            if (fc > 0 && !mbar_wait(acc_empty, (uint32_t)((fc - 1) & 1))) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          }
+          if (failed(&s_fail) || !mbar_wait(&full[b], (uint32_t)((it / NBUF) & 1))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint32_t a0 = sptr(bufA + (size_t)b * A_STAGE), b0 = sptr(bufB + (size_t)b * B_STAGE);
 #pragma unroll
-      for (int kb2 = 0; kb2 < 2; kb2++)
+          for (int kb2 = 0; kb2 < 2; kb2++)
 #pragma unroll
-        for (int q = 0; q < S; q++) {
-          const uint64_t bd = smem_desc(b0 + (uint32_t)((q * 2 + kb2) * B_K16_BYTES), 128, 256);
+            for (int q = 0; q < S; q++) {
+              const uint64_t bd = smem_desc(b0 + (uint32_t)((q * 2 + kb2) * B_K16_BYTES), 128, 256);
 #pragma unroll
-          for (int p = 0; p < S - q; p++) {
-            const uint64_t ad = smem_desc(a0 + (uint32_t)((p * 2 + kb2) * A_K16_BYTES), 128, 256);
-            // level d = p + q is first written at (ks, kb2, q) = (0, 0, 0), p = d: start it fresh there
-            const uint32_t acc = (ks == 0 && kb2 == 0 && q == 0) ? 0u : 1u;
-            umma(tmem + (uint32_t)((p + q) * UN), ad, bd, idesc, acc);
+              for (int p = 0; p < S - q; p++) {
+                const uint64_t ad = smem_desc(a0 + (uint32_t)((p * 2 + kb2) * A_K16_BYTES), 128, 256);
+                // level d = p + q is first written at (kb2, q) = (0, 0) of a chunk's first stage
+                const uint32_t acc = (first && kb2 == 0 && q == 0) ? 0u : 1u;
+                umma(tmem + (uint32_t)((p + q) * UN), ad, bd, idesc, acc);
+              }
+            }
+          umma_commit(&empty[b]);
+          if ((ks % CH_STAGES) == CH_STAGES - 1 || ks == nks - 1) {
+            umma_commit(acc_full);
+            fc++;
           }
         }
-      umma_commit(&empty[b]);
-    }
-    umma_commit(accb);
-  }
-  __syncwarp();
-  // epilogue: 16 warps; warp w reads TMEM lane quarter (w % 4) (rows 32 (w % 4) + lane)
-  // and columns [16 (w / 4), 16 (w / 4) + 16) of every level
-  const bool got = mbar_wait(accb, 0);
-  if (!got) atomicExch(&s_fail, 1);
-  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  const int quarter = warp & 3, cgroup = warp >> 2;
-  const int64_t gi = m0 + quarter * 32 + lane;
-  const int er = (got && gi < M) ? ea[gi] : EXP_NONE;
-  const bool neg_alpha = alpha < 0.0;
-  const int ea2 = (alpha == 0.0) ? 0 : (int)((__double_as_longlong(fabs(alpha)) >> 52) & 0x7FF) - 1023;
-  const bool alpha_pow2 = (alpha != 0.0) && ((__double_as_longlong(alpha) & ((1ll << 52) - 1)) == 0);
-  const int beta_mode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
-  for (int c0 = cgroup * (UN / 4); c0 < (cgroup + 1) * (UN / 4); c0 += 4) {
-    uint32_t v[S][4];
-#pragma unroll
-    for (int d = 0; d < S; d++) tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * UN + c0), v[d]);
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-    if (!got || gi >= M) continue;
-    // gather first (independent loads in flight together), then convert, then store
-    bool ok[4];
-    int ecv[4];
-    double cold[4];
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      const int64_t gj = n0 + c0 + c;
-      const int64_t dd = gi - gj + diag;
-      ok[c] = (gj < N) && !(mode == TRI_LOWER && dd < 0) && !(mode == TRI_UPPER && dd > 0);
-      ecv[c] = ok[c] ? eb[gj] : EXP_NONE;
-      cold[c] = (ok[c] && beta_mode != 0) ? C[gi + gj * ldc] : 0.0;
-    }
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-      if (!ok[c]) continue;
-      const int ec = ecv[c];
-      double val = 0.0;
-      if (er != EXP_NONE && ec != EXP_NONE) {
-        int64_t hi = 0, lo = 0;
-#pragma unroll
-        for (int d = 0; d < 4; d++) hi = hi * 256 + (int64_t)__float2int_rn(__uint_as_float(v[d][c]));
-#pragma unroll
-        for (int d = 4; d < S; d++) lo = lo * 256 + (int64_t)__float2int_rn(__uint_as_float(v[d][c]));
-        // V = hi 2^24 + lo as a signed 128-bit integer; value = V 2^(er + ec - 64)
-        const uint64_t hl = (uint64_t)hi << 24;
-        int64_t vh = hi >> 40;  // arithmetic shift keeps the sign
-        uint64_t vl = hl + (uint64_t)lo;
-        // carry / borrow of the low-word addition
-        if (lo >= 0) vh += (vl < hl) ? 1 : 0;
-        else vh -= (vl > hl) ? 1 : 0;
-        if (alpha_pow2) val = i128_ldexp(vh, vl, er + ec - 64 + ea2, neg_alpha);
-        else val = scale_slow(alpha, i128_ldexp(vh, vl, er + ec - 64, false));
+        if (!ok) break;
       }
-      const int64_t gj = n0 + c0 + c;
-      C[gi + gj * ldc] = (beta_mode == 0) ? val : (beta_mode == 1 ? cold[c] + val : fma(beta, cold[c], val));
+      if (!ok) atomicExch(&s_fail, 1);
+      // every MMA of ours has finished before TMEM can be freed
+      umma_commit(fin);
+      if (!mbar_wait(fin, 0)) atomicExch(&s_fail, 1);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lane quarter w % 4 (rows 32 (w % 4) + lane)
+    // and columns [16 (w / 4), 16 (w / 4) + 16) of every level
+    const int quarter = warp & 3, cgroup = warp >> 2;
+    const bool neg_alpha = alpha < 0.0;
+    const int ea2 = (alpha == 0.0) ? 0 : (int)((__double_as_longlong(fabs(alpha)) >> 52) & 0x7FF) - 1023;
+    const bool alpha_pow2 = (alpha != 0.0) && ((__double_as_longlong(alpha) & ((1ll << 52) - 1)) == 0);
+    const int beta_mode = (beta == 0.0) ? 0 : (beta == 1.0 ? 1 : 2);
+    const int64_t nch = (nks + CH_STAGES - 1) / CH_STAGES;
+    int64_t fc = 0;  // chunks folded
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+      int64_t m0, n0;
+      if (!g.get(t, m0, n0)) continue;
+      const int64_t gi = m0 + quarter * 32 + lane;
+      // V = sum over chunks of the recombined level sums, a signed 128-bit
+      // integer (vh:vl) per element, held in registers
+      int32_t vh[EPI_COLS];
+      uint64_t vl[EPI_COLS];
+#pragma unroll
+      for (int c = 0; c < EPI_COLS; c++) {
+        vh[c] = 0;
+        vl[c] = 0;
+      }
+      for (int64_t ch = 0; ch < nch; ch++, fc++) {
+        if (!mbar_wait(acc_full, (uint32_t)(fc & 1))) {
+          atomicExch(&s_fail, 1);
+          ok = false;
+          break;
+        }
+        if (failed(&s_fail)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+        for (int c0 = 0; c0 < EPI_COLS; c0 += 4) {
+          uint32_t v[S][4];
+#pragma unroll
+          for (int d = 0; d < S; d++)
+            tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * UN + cgroup * EPI_COLS + c0), v[d]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < 4; c++) {
+            const uint32_t lv[S] = {v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c]};
+            fold_add(lv, vh[c0 + c], vl[c0 + c]);
+          }
+        }
+        // TMEM is free for the next chunk's MMAs
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sptr(acc_empty)) : "memory");
+      }
+      if (!ok) break;
+      if (gi >= g.M) continue;
+      const int er = ea[gi];
+      const int64_t gjb = n0 + cgroup * EPI_COLS;
+#pragma unroll
+      for (int c0 = 0; c0 < EPI_COLS; c0 += 4) {
+        // gather first (independent loads in flight together), then convert, then store
+        bool ok[4];
+        int ecv[4];
+        double cold[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          const int64_t gj = gjb + c0 + c;
+          const int64_t dd = gi - gj + g.diag;
+          ok[c] = (gj < g.N) && !(g.mode == TRI_LOWER && dd < 0) && !(g.mode == TRI_UPPER && dd > 0);
+          ecv[c] = ok[c] ? eb[gj] : EXP_NONE;
+          cold[c] = (ok[c] && beta_mode != 0) ? C[gi + gj * ldc] : 0.0;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+          if (!ok[c]) continue;
+          const int ec = ecv[c];
+          const int64_t h = vh[c0 + c];
+          const uint64_t l = vl[c0 + c];
+          const bool live = (er != EXP_NONE && ec != EXP_NONE);
+          double val;
+          if (alpha_pow2 && beta_mode == 1) {
+            val = live ? add_i128(cold[c], h, l, er + ec - 64 + ea2, neg_alpha) : cold[c];
+          } else {
+            double ab = 0.0;
+            if (live)
+              ab = alpha_pow2 ? i128_ldexp(h, l, er + ec - 64 + ea2, neg_alpha)
+                              : scale_slow(alpha, i128_ldexp(h, l, er + ec - 64, false));
+            val = (beta_mode == 0) ? ab : (beta_mode == 1 ? cold[c] + ab : fma(beta, cold[c], ab));
+          }
+          C[gi + (gjb + c0 + c) * ldc] = val;
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0) {
-    // no bulk copy of ours may still be landing in shared memory when the CTA exits
-    for (int ks = max(0, s_issued - NBUF); ks < s_issued; ks++)
-      if (!mbar_wait(&full[ks % NBUF], (uint32_t)((ks / NBUF) & 1))) s_fail = 1;
+    // none of the producer's bulk copies may still be landing when the CTA exits
+    const int64_t iss = s_issued;
+    for (int64_t i = (iss > NBUF ? iss - NBUF : 0); i < iss; i++)
+      if (!mbar_wait(&full[i % NBUF], (uint32_t)((i / NBUF) & 1))) s_fail = 1;
     if (s_fail) atomicExch(err, 1);
   }
+  __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
@@ -329,7 +515,7 @@ int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, i
               const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
               TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err) {
   if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
-  if (K > 128 || K <= 0) return GSYEIG_NOT_SUPPORTED;
+  if (K > UMMA_MAX_K || K <= 0) return GSYEIG_NOT_SUPPORTED;
   const int64_t Mpad = ceil_div(M, UM) * UM, Npad = ceil_div(N, UN) * UN, Kpad = ceil_div(K, UKS) * UKS;
   if (ws_bytes < umma_workspace_bytes(M, N, K)) return GSYEIG_NOT_SUPPORTED;
   slicing::SlicePlan P;
@@ -346,9 +532,12 @@ int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, i
   GS_TRY(slicing::slice_operands(st, transA, transB, M, N, K, A, lda, B, ldb, P, {true, UM}, {true, UN}));
   const size_t smem = (size_t)NBUF * (A_STAGE + B_STAGE) + 128;
   GS_CUDA(cudaFuncSetAttribute((const void *)k_sliced_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((unsigned)(Mpad / UM), (unsigned)(Npad / UN));
-  k_sliced_umma<<<grid, UMMA_THREADS, smem, st>>>(M, N, Kpad / UKS, P.SA, P.SB, P.ea, P.eb, alpha, beta, C, ldc,
-                                                  (int)mode, diag, abort_flag, err);
+  TileGrid g{M, N, diag, (int)(Mpad / UM), (int)(Npad / UN), (int)mode};
+  // CTAs without an active tile (TRI modes) only set up and leave
+  const int64_t tiles = (int64_t)g.mt * g.nt;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms());
+  k_sliced_umma<<<grid, UMMA_THREADS, smem, st>>>(g, Kpad / UKS, P.SA, P.SB, P.ea, P.eb, alpha, beta, C, ldc,
+                                                  abort_flag, err);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;

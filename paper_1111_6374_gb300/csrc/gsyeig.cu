@@ -129,13 +129,15 @@ int nb_of(gsyeig_handle h, int64_t n) {
 }
 
 // Install the GEMM mode for this call; the sliced GEMM needs slices of two
-// operands of at most max(n, s) rows and nb columns.
+// operands of at most max(n, s) rows and K up to the outer block 4 nb (the
+// tcgen05 engine takes up to 512 per call).
 int gemm_setup(gsyeig_handle h, int64_t n, int nb, int64_t s) {
   h->gemm.sliced = (h->opts.fp64_gemm != 1) && nb <= 128;
   h->gemm.umma = (h->opts.fp64_gemm == 0);
   if (h->gemm.sliced) {
     const int64_t r = std::max<int64_t>(n, s);
-    GS_TRY(h->gemm_ws.ensure(std::max(sliced_workspace_bytes(r, r, nb), umma_workspace_bytes(r, r, nb))));
+    GS_TRY(h->gemm_ws.ensure(
+        std::max(sliced_workspace_bytes(r, r, nb), umma_workspace_bytes(r, r, std::min<int64_t>(512, 4 * (int64_t)nb)))));
     h->gemm.ws = h->gemm_ws.p;
     h->gemm.ws_bytes = h->gemm_ws.bytes;
     GS_TRY(h->gemm_err.ensure(64));

@@ -277,18 +277,31 @@ def test_no_convergence_and_timeout_statuses():
     assert info["status"] == 3
 
 
-def test_full_size_workload_properties(solver):
+@pytest.mark.parametrize("inverse", [1, 0], ids=["inverse-route", "direct-route"])
+def test_full_size_workload_properties(inverse):
     """n = 16384, s = 100 smallest (the benchmark workload): every pair is
     checked against the constructed spectrum, the backward error and
-    B-orthonormality (the oracle cannot run at this size in test time)."""
+    B-orthonormality (the oracle cannot run at this size in test time).
+
+    The benchmark's route (inverse problem, Section 3.1) meets the 1e-10
+    relative eigenvalue bound for every pair.  On the direct route the
+    smallest lambda (~5e-3 here, against ||C|| = 1000) is limited by the
+    backward error of C itself (Weyl: |d lambda| <= ||dC|| ~ eps ||C||), so
+    there the bound is 1e-10 |lambda| + 1e-14 ||C||."""
+    from paper_1111_6374_gb300 import Solver
+
     n, s = 16384, 100
     A, B, lam = inputs.make_pencil(n, seed=0, device="cuda")
-    w, X, info = solver.solve(A, B, s)
-    assert info["nconv"] >= s
+    w, X, info = Solver(0, inverse=inverse).solve(A, B, s)
+    assert info["nconv"] >= s and info["inverse"] == inverse
     lam_s = lam[:s]
-    assert float(((w - lam_s).abs() / lam_s.abs()).max()) <= 1e-10
+    err = (w - lam_s).abs()
+    if inverse:
+        assert float((err / lam_s.abs()).max()) <= 1e-10
+    else:
+        assert bool((err <= 1e-10 * lam_s.abs() + 1e-14 * float(lam.abs().max())).all()), float(err.max())
     # backward errors on the GPU in float64 (torch matmul used as a checker)
-    nA = float(torch.linalg.matrix_norm(A, ord=2)) if n <= 4096 else _power(A)
+    nA = _power(A)
     nB = _power(B)
     R = A @ X - (B @ X) * w
     et = R.norm(dim=0) / ((nA + w.abs() * nB) * X.norm(dim=0))
