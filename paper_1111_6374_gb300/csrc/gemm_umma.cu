@@ -3,13 +3,13 @@
 // how the 28 digit-pair products are issued and how the exact level sums are
 // turned into FP64).
 //
-//  * Operands are pre-split by k_split_umma straight into the UMMA
+//  * Operands are pre-split by k_split straight into the UMMA
 //    "no-swizzle K-major" core-matrix layout (8 rows x 16 bytes per core
 //    matrix, K-adjacent cores 128 B apart, row-adjacent cores 256 B apart),
-//    grouped so that one K stage (32 k) of all 7 slices of a 128-row A block
-//    (56 KB) or a 64-row B block (28 KB) is one contiguous run: each stage is
-//    brought in by a single cp.async.bulk per operand, completing on an
-//    mbarrier (no tensor map needed).
+//    grouped so that one K stage (32 k: two k16 blocks of all 7 slices) of a
+//    128-row A block (56 KB) or a 64-row B block (28 KB) is one contiguous
+//    run: each stage is brought in by a single cp.async.bulk per operand into
+//    a 2-deep ring, completing on an mbarrier (no tensor map needed).
 //  * Persistent CTAs (one per SM) walk the 128 x 64 tiles of C with
 //    warp-specialised roles: a producer lane, an MMA lane and 16 epilogue
 //    warps.  One thread issues tcgen05.mma.kind::f16 (bf16 x bf16 -> fp32,
@@ -21,9 +21,9 @@
 //    columns each) reads the 7 level sums with tcgen05.ld, recombines them
 //    exactly into a 128-bit integer per element added to a register
 //    accumulator, and hands TMEM back to the next chunk's MMAs; after the
-//    last chunk C += V 2^e is added and rounded in integer arithmetic (a
-//    correctly rounded integer-only conversion to FP64 with the row/column
-//    exponents folded in): GB300's narrow FP64 pipe is not used.
+//    last chunk the exact sum V, scaled by the row and column exponents, is
+//    faithfully rounded to FP64 in integer arithmetic and added to C with
+//    one FP64 add.
 //  * Every mbarrier wait is bounded; on expiry the kernel records the fault
 //    in *err, still waits (bounded) for its own copies, frees its TMEM and
 //    returns.
@@ -37,10 +37,12 @@ namespace {
 using slicing::S;
 using slicing::EXP_NONE;
 constexpr int UM = 128, UN = 64, UKS = 32;  // tile rows, tile cols, K per stage
+constexpr int KB2 = UKS / 16;                // k16 blocks per stage
+constexpr int KPAD = 32;                     // K padding of the digit planes
 constexpr int A_K16_BYTES = UM * 16 * 2;     // one slice, one k16 block: 4096
 constexpr int B_K16_BYTES = UN * 16 * 2;     // 2048
-constexpr int A_STAGE = S * 2 * A_K16_BYTES; // 57344
-constexpr int B_STAGE = S * 2 * B_K16_BYTES; // 28672
+constexpr int A_STAGE = KB2 * S * A_K16_BYTES;  // 57344
+constexpr int B_STAGE = KB2 * S * B_K16_BYTES;  // 28672
 constexpr int NBUF = 2;
 constexpr int CH_STAGES = 128 / UKS;  // K stages per exact chunk (level sums exact for K <= 128)
 constexpr int UMMA_MAX_K = 512;
@@ -116,6 +118,10 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// The registers written by tcgen05.ld are valid only after tcgen05.wait::ld;
+// this empty asm makes every later use depend on a point after the wait.
+__device__ __forceinline__ void reg_fence(uint32_t &x) { asm volatile("" : "+r"(x)); }
+
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
@@ -176,60 +182,32 @@ __device__ __forceinline__ double i128_ldexp(int64_t h, uint64_t l, int e2, bool
   return __longlong_as_double((long long)bits);
 }
 
-// Out-of-line FP64 form of c + (-1)^flip V 2^e2 for the cases the integer
-// path below does not take (c subnormal, infinite or NaN, or c far below the
-// product's last bit).
-__device__ __noinline__ double add_slow(double c, int64_t h, uint64_t l, int e2, bool flip) {
-  return c + i128_ldexp(h, l, e2, flip);
-}
-
-// c + (-1)^flip V 2^e2 (V = h:l, |V| < 2^73) correctly rounded, in integer
-// arithmetic: both terms are aligned on the lower of their last-bit
-// exponents and added exactly in 128 bits, then rounded once.  With c's
-// last bit at 2^ec (c = +-mc 2^ec, mc < 2^53) and sh = ec - e2:
-//   sh > 72:        |V 2^e2| < 2^(e2+73) <= ulp(c)/2, the sum rounds to c;
-//   0 <= sh <= 72:  c 2^-e2 = mc 2^sh < 2^125, the sum fits in 127 bits;
-//   -54 <= sh < 0:  V 2^-sh < 2^127, the sum fits with its last bit at 2^ec;
-//   sh < -54:       the FP64 path.
-__device__ __forceinline__ double add_i128(double c, int64_t h, uint64_t l, int e2, bool flip) {
-  if (h == 0 && l == 0) return c;
-  const uint64_t cb = (uint64_t)__double_as_longlong(c);
-  const int ce = (int)((cb >> 52) & 0x7FF);
-  if ((cb << 1) == 0) return i128_ldexp(h, l, e2, flip);  // c = +-0
-  if (ce == 0 || ce == 0x7FF) return add_slow(c, h, l, e2, flip);
-  const int sh = (ce - 1075) - e2;
-  if (sh > 72) return c;
-  if (sh < -54) return add_slow(c, h, l, e2, flip);
-  if (flip) {  // V <- -V
-    l = ~l + 1;
-    h = (int64_t)(~(uint64_t)h + (l == 0 ? 1 : 0));
-  }
-  const uint64_t mc = (cb & ((1ull << 52) - 1)) | (1ull << 52);
-  uint64_t th, tl;  // aligned magnitude of c
-  uint64_t vh = (uint64_t)h, vl = l;
-  int e;
-  if (sh >= 0) {
-    tl = (sh < 64) ? (mc << sh) : 0;
-    th = (sh == 0) ? 0 : (sh < 64 ? (mc >> (64 - sh)) : (mc << (sh - 64)));
-    e = e2;
-  } else {
-    const int k = -sh;  // shift V left by k (1..54)
-    vh = (vh << k) | (vl >> (64 - k));
-    vl <<= k;
-    tl = mc;
-    th = 0;
-    e = ce - 1075;
-  }
-  if (cb >> 63) {  // subtract |c|
-    const uint64_t nl = vl - tl;
-    vh = vh - th - (vl < tl ? 1 : 0);
-    vl = nl;
-  } else {
-    const uint64_t nl = vl + tl;
-    vh = vh + th + (nl < vl ? 1 : 0);
-    vl = nl;
-  }
-  return i128_ldexp((int64_t)vh, vl, e, false);
+// (-1)^flip V 2^e2 for V = h:l, |V| < 2^73, faithfully rounded to a double
+// (error < 1 ulp) in 64-bit integer arithmetic, branch-free so that the
+// elements of a thread interleave: T = V >> 10 fits in an int64 and carries
+// every bit a double keeps (the 10 bits shifted out can only move a rounding
+// tie).  *slow is set when the result leaves the normal range (the caller
+// then takes i128_ldexp).  GB300 runs FP64 adds at about 1.6 per clock per
+// SM and integer-to-float conversions at 16, so the C update is this, plus
+// one FP64 add.
+__device__ __forceinline__ double i128_to_double(int32_t h, uint64_t l, int e2, bool flip, bool &slow) {
+  const int64_t T = (int64_t)(((uint64_t)(int64_t)h << 54) | (l >> 10));
+  const bool neg = (T < 0) != flip;
+  const uint64_t a = (uint64_t)(T < 0 ? -T : T);
+  const bool zero = a == 0;
+  const int lz = __clzll((long long)a);
+  const uint64_t w = a << (lz & 63);
+  uint64_t mant = w >> 11;
+  const uint64_t rbits = w & 0x7FF;
+  const bool up = (rbits & 0x400) && ((rbits & 0x3FF) || (mant & 1));
+  mant += up ? 1ull : 0ull;
+  const int carry = (int)(mant >> 53);
+  mant >>= carry;
+  const int be = (63 - lz) + e2 + 10 + carry + 1023;
+  slow = !zero && (be <= 0 || be >= 2047);
+  const double r = __longlong_as_double(
+      (long long)(((uint64_t)neg << 63) | ((uint64_t)(be & 0x7FF) << 52) | (mant & ((1ull << 52) - 1))));
+  return zero ? 0.0 : r;
 }
 
 // Persistent CTAs, one per SM; tile t = blockIdx.x + i gridDim.x over the
@@ -249,6 +227,7 @@ constexpr int EPI_WARPS = 16;
 constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
 constexpr int UMMA_THREADS = (EPI_WARPS + 2) * 32;
 constexpr int EPI_COLS = UN / (EPI_WARPS / 4);  // columns of a tile per epilogue warp (16)
+constexpr int UPD = 2;  // elements a thread updates together
 
 // Exact integer value of a level sum (an integer-valued fp32, |x| < 2^24).
 __device__ __forceinline__ int32_t lvl(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
@@ -372,13 +351,13 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           const uint32_t a0 = sptr(bufA + (size_t)b * A_STAGE), b0 = sptr(bufB + (size_t)b * B_STAGE);
 #pragma unroll
-          for (int kb2 = 0; kb2 < 2; kb2++)
+          for (int kb2 = 0; kb2 < KB2; kb2++)
 #pragma unroll
             for (int q = 0; q < S; q++) {
-              const uint64_t bd = smem_desc(b0 + (uint32_t)((q * 2 + kb2) * B_K16_BYTES), 128, 256);
+              const uint64_t bd = smem_desc(b0 + (uint32_t)((kb2 * S + q) * B_K16_BYTES), 128, 256);
 #pragma unroll
               for (int p = 0; p < S - q; p++) {
-                const uint64_t ad = smem_desc(a0 + (uint32_t)((p * 2 + kb2) * A_K16_BYTES), 128, 256);
+                const uint64_t ad = smem_desc(a0 + (uint32_t)((kb2 * S + p) * A_K16_BYTES), 128, 256);
                 // level d = p + q is first written at (kb2, q) = (0, 0) of a chunk's first stage
                 const uint32_t acc = (first && kb2 == 0 && q == 0) ? 0u : 1u;
                 umma(tmem + (uint32_t)((p + q) * UN), ad, bd, idesc, acc);
@@ -412,6 +391,10 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
       int64_t m0, n0;
       if (!g.get(t, m0, n0)) continue;
       const int64_t gi = m0 + quarter * 32 + lane;
+      const int64_t gjb = n0 + cgroup * EPI_COLS;
+      // the exponents this thread needs: its row's, and lane j < 16 holds column gjb + j's
+      const int er_pre = (gi < g.M) ? ea[gi] : EXP_NONE;
+      const int ec_pre = (lane < EPI_COLS && gjb + lane < g.N) ? eb[gjb + lane] : EXP_NONE;
       // V = sum over chunks of the recombined level sums, a signed 128-bit
       // integer (vh:vl) per element, held in registers
       int32_t vh[EPI_COLS];
@@ -440,6 +423,10 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * UN + cgroup * EPI_COLS + c0), v[d]);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
+          for (int d = 0; d < S; d++)
+#pragma unroll
+            for (int c = 0; c < 4; c++) reg_fence(v[d][c]);
+#pragma unroll
           for (int c = 0; c < 4; c++) {
             const uint32_t lv[S] = {v[0][c], v[1][c], v[2][c], v[3][c], v[4][c], v[5][c], v[6][c]};
             fold_add(lv, vh[c0 + c], vl[c0 + c]);
@@ -451,41 +438,51 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sptr(acc_empty)) : "memory");
       }
       if (!ok) break;
-      if (gi >= g.M) continue;
-      const int er = ea[gi];
-      const int64_t gjb = n0 + cgroup * EPI_COLS;
+      const bool row_ok = gi < g.M;  // (no early exit: the warp shuffles below need every lane)
+      const int er = er_pre;
 #pragma unroll
-      for (int c0 = 0; c0 < EPI_COLS; c0 += 4) {
+      for (int c0 = 0; c0 < EPI_COLS; c0 += UPD) {
         // gather first (independent loads in flight together), then convert, then store
-        bool ok[4];
-        int ecv[4];
-        double cold[4];
+        bool ok[UPD];
+        int ecv[UPD];
+        double cold[UPD];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
+        for (int c = 0; c < UPD; c++) {
           const int64_t gj = gjb + c0 + c;
           const int64_t dd = gi - gj + g.diag;
-          ok[c] = (gj < g.N) && !(g.mode == TRI_LOWER && dd < 0) && !(g.mode == TRI_UPPER && dd > 0);
-          ecv[c] = ok[c] ? eb[gj] : EXP_NONE;
+          ok[c] = row_ok && (gj < g.N) && !(g.mode == TRI_LOWER && dd < 0) && !(g.mode == TRI_UPPER && dd > 0);
+          const int ecs = __shfl_sync(0xffffffffu, ec_pre, c0 + c);
+          ecv[c] = ok[c] ? ecs : EXP_NONE;
           cold[c] = (ok[c] && beta_mode != 0) ? C[gi + gj * ldc] : 0.0;
         }
+        if (alpha_pow2 && beta_mode != 2) {
+          // the solver's updates: C = +-2^k A B (+ C): V rounded to FP64
+          // (branch-free), then one FP64 add
+          double val[UPD];
+          bool slow[UPD];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-          if (!ok[c]) continue;
-          const int ec = ecv[c];
-          const int64_t h = vh[c0 + c];
-          const uint64_t l = vl[c0 + c];
-          const bool live = (er != EXP_NONE && ec != EXP_NONE);
-          double val;
-          if (alpha_pow2 && beta_mode == 1) {
-            val = live ? add_i128(cold[c], h, l, er + ec - 64 + ea2, neg_alpha) : cold[c];
-          } else {
-            double ab = 0.0;
-            if (live)
-              ab = alpha_pow2 ? i128_ldexp(h, l, er + ec - 64 + ea2, neg_alpha)
-                              : scale_slow(alpha, i128_ldexp(h, l, er + ec - 64, false));
-            val = (beta_mode == 0) ? ab : (beta_mode == 1 ? cold[c] + ab : fma(beta, cold[c], ab));
+          for (int c = 0; c < UPD; c++) {
+            const bool live = (er != EXP_NONE && ecv[c] != EXP_NONE);
+            val[c] = i128_to_double(live ? vh[c0 + c] : 0, live ? vl[c0 + c] : 0ull, er + ecv[c] - 64 + ea2,
+                                    neg_alpha, slow[c]);
           }
-          C[gi + (gjb + c0 + c) * ldc] = val;
+#pragma unroll
+          for (int c = 0; c < UPD; c++) {
+            if (!ok[c]) continue;
+            if (slow[c]) val[c] = i128_ldexp(vh[c0 + c], vl[c0 + c], er + ecv[c] - 64 + ea2, neg_alpha);
+            C[gi + (gjb + c0 + c) * ldc] = (beta_mode == 0) ? val[c] : cold[c] + val[c];
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < UPD; c++) {
+            if (!ok[c]) continue;
+            const int ec = ecv[c];
+            double ab = 0.0;
+            if (er != EXP_NONE && ec != EXP_NONE)
+              ab = alpha_pow2 ? i128_ldexp(vh[c0 + c], vl[c0 + c], er + ec - 64 + ea2, neg_alpha)
+                              : scale_slow(alpha, i128_ldexp(vh[c0 + c], vl[c0 + c], er + ec - 64, false));
+            C[gi + (gjb + c0 + c) * ldc] = (beta_mode == 0) ? ab : (beta_mode == 1 ? cold[c] + ab : fma(beta, cold[c], ab));
+          }
         }
       }
     }
@@ -506,7 +503,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
 }  // namespace
 
 size_t umma_workspace_bytes(int64_t M, int64_t N, int64_t K) {
-  const int64_t Mpad = ceil_div(M, UM) * UM, Npad = ceil_div(N, UN) * UN, Kpad = ceil_div(K, UKS) * UKS;
+  const int64_t Mpad = ceil_div(M, UM) * UM, Npad = ceil_div(N, UN) * UN, Kpad = ceil_div(K, KPAD) * KPAD;
   return (size_t)S * (size_t)(Mpad + Npad) * (size_t)Kpad * 2 + slicing::slice_ints(Mpad, Npad, Kpad) * sizeof(int) +
          4096;
 }
@@ -516,7 +513,7 @@ int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, i
               TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err) {
   if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
   if (K > UMMA_MAX_K || K <= 0) return GSYEIG_NOT_SUPPORTED;
-  const int64_t Mpad = ceil_div(M, UM) * UM, Npad = ceil_div(N, UN) * UN, Kpad = ceil_div(K, UKS) * UKS;
+  const int64_t Mpad = ceil_div(M, UM) * UM, Npad = ceil_div(N, UN) * UN, Kpad = ceil_div(K, KPAD) * KPAD;
   if (ws_bytes < umma_workspace_bytes(M, N, K)) return GSYEIG_NOT_SUPPORTED;
   slicing::SlicePlan P;
   P.Mpad = Mpad;

@@ -50,14 +50,13 @@ __device__ __forceinline__ size_t digit_off(const DigitLayout &L, int p, int64_t
                                             int64_t Kpad) {
   if (!L.umma) return (((size_t)p * Rpad + r) * Kpad + k) * 2;
   const int rb = L.rb;
-  const int64_t nks = Kpad / 32;
+  const int64_t nks = Kpad / 16;  // one stage = one k16 block of all S slices
   const int64_t blk = r / rb, ii = r % rb;
-  const int64_t ks = k / 32, kk = k % 32;
-  const int kb2 = (int)(kk / 16), k16 = (int)(kk % 16);
+  const int64_t ks = k / 16;
+  const int k16 = (int)(k % 16);
   const int ki = k16 / 8, kc = k16 % 8, mi = (int)(ii / 8), rr = (int)(ii % 8);
   const size_t k16bytes = (size_t)rb * 32;
-  return ((size_t)(blk * nks + ks) * S + p) * 2 * k16bytes + (size_t)kb2 * k16bytes + (size_t)mi * 256 + ki * 128 +
-         rr * 16 + kc * 2;
+  return ((size_t)(blk * nks + ks) * S + p) * k16bytes + (size_t)mi * 256 + ki * 128 + rr * 16 + kc * 2;
 }
 
 __global__ void k_fill(int n, int *p, int v) {
