@@ -137,6 +137,7 @@ struct FactorWork {
   double *panel = nullptr;  // staging buffer, max(nb, ...) x n
   size_t panel_elems = 0;
   int *flag = nullptr;      // device int: first failed pivot (1-based) or 0
+  double *rdiag = nullptr;  // device, nb entries: 1 / U(i, i) of the diagonal block just factored
 };
 
 int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, FactorWork &w);

@@ -24,32 +24,28 @@ struct SmemBlock {
   __device__ double &operator()(int i, int j) { return p[i + j * ld]; }
 };
 
-// Inverse of the upper-triangular kb x kb block S (in shared memory) into
-// the global nb x nb block `out` (ld nb, zeros below the diagonal): each
-// thread owns whole columns c and back-substitutes U x = e_c upwards, so no
-// thread reads another thread's output.
-__device__ void upper_inverse(SmemBlock S, double *out, int nb, int kb) {
-  for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-    double *x = out + (size_t)c * nb;
-    for (int i = nb - 1; i > c || (c >= kb && i >= 0); i--) x[i] = 0.0;
-    if (c >= kb) continue;
-    x[c] = 1.0 / S(c, c);
-    for (int i = c - 1; i >= 0; i--) {
-      double t = 0.0;
-      for (int k = i + 1; k <= c; k++) t = fma(S(i, k), x[k], t);
-      x[i] = -t / S(i, i);
-    }
-  }
+// 1/d to within an ulp: FP32 seed, two Newton steps in FP64 (GB300's FP64
+// divide is a long dependent sequence on a narrow pipe).
+__device__ __forceinline__ double recip(double d) {
+  double r = (double)(1.0f / (float)d);
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
 }
 
 // Factor the diagonal block B[k0:k0+kb, k0:k0+kb] (upper triangle) in
-// place, B_kk = U_kk^T U_kk, then store U_kk^-1 (kb x kb, ld nb, zeros below
-// the diagonal) in Uinv.  A non-positive or NaN pivot records its global
-// 1-based index in *flag and stops.
+// place, B_kk = U_kk^T U_kk, and leave 1 / U_kk(i, i) in rdiag[0..kb).
+// Right-looking on the unscaled rows, A'(r, c) = A(r, c) - A(j, r) A(j, c) /
+// A(j, j): each step needs one reciprocal (computed by every thread that
+// uses it, so no serial section), and the square roots are applied to all
+// rows at the end in parallel, U(j, c) = A(j, c) / sqrt(A(j, j)).  A
+// non-positive or NaN pivot records its global 1-based index in *flag and
+// stops.
 __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(double *B, int64_t ldb, int64_t k0, int kb, int nb,
-                                                             double *Uinv, int *flag) {
+                                                             double *rdiag, int *flag) {
   extern __shared__ double smem[];
-  __shared__ int s_bad;
+  double *v = smem + (size_t)(nb + 1) * nb;  // scaled pivot row A(j, c) / A(j, j)
   if (*flag) return;
   SmemBlock S{smem, nb + 1};
   const int t = threadIdx.x;
@@ -57,57 +53,103 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(double *B, int64_t 
     int i = idx % kb, j = idx / kb;
     S(i, j) = (i <= j) ? B[GS_IDX(k0 + i, k0 + j, ldb)] : 0.0;
   }
-  if (t == 0) s_bad = 0;
   __syncthreads();
+  int bad = 0;
   for (int j = 0; j < kb; j++) {
-    if (t == 0) {
-      double d = S(j, j);
-      if (!(d > 0.0)) {
-        s_bad = (int)(k0 + j + 1);
-      } else {
-        S(j, j) = sqrt(d);
-      }
+    const double d = S(j, j);  // every thread reads the same pivot: a uniform exit
+    if (!(d > 0.0)) {
+      bad = (int)(k0 + j + 1);
+      break;
     }
+    const int w = kb - j - 1;
+    if (t < w) v[t] = S(j, j + 1 + t) * recip(d);
     __syncthreads();
-    if (s_bad) break;
-    double piv = S(j, j);
-    for (int c = j + 1 + t; c < kb; c += blockDim.x) S(j, c) /= piv;
-    __syncthreads();
-    // trailing update of the upper triangle: S(r, c) -= S(j, r) S(j, c), j < r <= c
-    int w = kb - j - 1;
+    // trailing update of the upper triangle: A(r, c) -= A(j, r) v(c), j < r <= c
     for (int idx = t; idx < w * w; idx += blockDim.x) {
-      int r = j + 1 + idx % w, c = j + 1 + idx / w;
-      if (r <= c) S(r, c) = fma(-S(j, r), S(j, c), S(r, c));
+      const int r = idx % w, c = idx / w;
+      if (r <= c) S(j + 1 + r, j + 1 + c) = fma(-S(j, j + 1 + r), v[c], S(j + 1 + r, j + 1 + c));
     }
     __syncthreads();
   }
-  if (s_bad) {
-    if (t == 0) atomicCAS(flag, 0, s_bad);
+  if (bad) {
+    if (t == 0) atomicCAS(flag, 0, bad);
     return;
   }
-  upper_inverse(S, Uinv, nb, kb);
-  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
-    int i = idx % kb, j = idx / kb;
-    if (i <= j) B[GS_IDX(k0 + i, k0 + j, ldb)] = S(i, j);
-  }
-}
-
-// Inverse of every diagonal block of an upper-triangular U (one CTA each).
-__global__ void __launch_bounds__(DIAG_THREADS) k_trtri_diag(int64_t n, const double *U, int64_t ldu, int nb,
-                                                             double *Uinv) {
-  extern __shared__ double smem[];
-  SmemBlock S{smem, nb + 1};
-  const int64_t k0 = (int64_t)blockIdx.x * nb;
-  const int kb = (int)std::min<int64_t>(nb, n - k0);
-  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
-    int i = idx % kb, j = idx / kb;
-    S(i, j) = (i <= j) ? U[GS_IDX(k0 + i, k0 + j, ldu)] : 0.0;
+  // U(j, c) = A(j, c) / sqrt(A(j, j)) for c >= j
+  for (int j = t; j < kb; j += blockDim.x) {
+    const double sj = sqrt(S(j, j));
+    const double rs = 1.0 / sj;
+    rdiag[j] = rs;
+    v[j] = rs;
   }
   __syncthreads();
-  upper_inverse(S, Uinv + (size_t)blockIdx.x * nb * nb, nb, kb);
+  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
+    const int i = idx % kb, j = idx / kb;
+    if (i < j) B[GS_IDX(k0 + i, k0 + j, ldb)] = S(i, j) * v[i];
+    else if (i == j) B[GS_IDX(k0 + i, k0 + j, ldb)] = S(i, i) * v[i];
+  }
 }
 
-size_t diag_smem_bytes(int nb) { return (size_t)(nb + 1) * nb * sizeof(double); }
+// Inverses of upper-triangular kb x kb diagonal blocks into nb x nb blocks
+// of Uinv (ld nb, zeros below the diagonal), spread over many SMs: block
+// q = blockIdx.y starts at row/column q nb; each CTA stages that block of U in
+// shared memory and each of its warps back-substitutes one column c,
+// x_k = b_k / U(k, k), b_i -= U(i, k) x_k for i < k, with lane l holding
+// rows l, l + 32, ...: no reductions and no FP64 divides in the loop.
+// rdiag (or NULL: computed here) holds 1 / U(k, k) of block 0.
+constexpr int INV_WARPS = 16;
+__global__ void __launch_bounds__(INV_WARPS * 32) k_trtri_cols(int64_t n, const double *U, int64_t ldu, int64_t k0,
+                                                                int nb, const double *rdiag, double *Uinv,
+                                                                const int *flag) {
+  extern __shared__ double smem[];
+  if (flag && *flag) return;
+  SmemBlock S{smem, nb + 1};
+  double *ri = smem + (size_t)(nb + 1) * nb;
+  const int64_t b0 = k0 + (int64_t)blockIdx.y * nb;
+  const int kb = (int)((n - b0 < nb) ? n - b0 : nb);
+  double *X = Uinv + (size_t)blockIdx.y * nb * nb;
+  for (int idx = threadIdx.x; idx < kb * kb; idx += blockDim.x) {
+    const int i = idx % kb, j = idx / kb;
+    if (i <= j) S(i, j) = U[GS_IDX(b0 + i, b0 + j, ldu)];
+  }
+  for (int k = threadIdx.x; k < kb; k += blockDim.x)
+    ri[k] = (rdiag && blockIdx.y == 0) ? rdiag[k] : 1.0 / U[GS_IDX(b0 + k, b0 + k, ldu)];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * INV_WARPS + (threadIdx.x >> 5);
+  if (c >= nb) return;
+  double *x = X + (size_t)c * nb;
+  if (c >= kb) {
+    for (int i = lane; i < nb; i += 32) x[i] = 0.0;
+    return;
+  }
+  constexpr int MR = 5;  // rows per lane: nb <= 160
+  double b[MR];
+#pragma unroll
+  for (int m = 0; m < MR; m++) b[m] = (lane + 32 * m == c) ? 1.0 : 0.0;
+  for (int k = c; k >= 0; k--) {
+    const int mk = k >> 5;
+    double bk = 0.0;
+#pragma unroll
+    for (int m = 0; m < MR; m++)
+      if (m == mk) bk = b[m];
+    const double xk = __shfl_sync(0xffffffffu, bk, k & 31) * ri[k];
+#pragma unroll
+    for (int m = 0; m < MR; m++) {
+      const int i = lane + 32 * m;
+      if (i < k) b[m] = fma(-S(i, k), xk, b[m]);
+      else if (i == k) b[m] = xk;
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < MR; m++) {
+    const int i = lane + 32 * m;
+    if (i < nb) x[i] = (i <= c) ? b[m] : 0.0;
+  }
+}
+
+// shared memory of both diagonal-block kernels: the block plus one row
+size_t diag_smem_bytes(int nb) { return (size_t)(nb + 2) * nb * sizeof(double); }
 
 int set_smem(const void *fn, size_t bytes) {
   if (bytes > 48 * 1024) GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -118,8 +160,9 @@ int set_smem(const void *fn, size_t bytes) {
 
 int trtri_diag_blocks(cudaStream_t st, int64_t n, const double *U, int64_t ldu, int nb, double *Uinv) {
   size_t sm = diag_smem_bytes(nb);
-  GS_TRY(set_smem((const void *)k_trtri_diag, sm));
-  k_trtri_diag<<<(unsigned)ceil_div(n, nb), DIAG_THREADS, sm, st>>>(n, U, ldu, nb, Uinv);
+  GS_TRY(set_smem((const void *)k_trtri_cols, sm));
+  k_trtri_cols<<<dim3((unsigned)ceil_div(nb, INV_WARPS), (unsigned)ceil_div(n, nb)), INV_WARPS * 32, sm, st>>>(
+      n, U, ldu, 0, nb, nullptr, Uinv, nullptr);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
@@ -136,6 +179,7 @@ constexpr int kOuter = 4;
 int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, FactorWork &w) {
   size_t sm = diag_smem_bytes(nb);
   GS_TRY(set_smem((const void *)k_potrf_diag, sm));
+  GS_TRY(set_smem((const void *)k_trtri_cols, sm));
   GS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
   const int64_t NB = (int64_t)kOuter * nb;
   for (int64_t J0 = 0; J0 < n; J0 += NB) {
@@ -143,8 +187,11 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
     for (int64_t k0 = J0; k0 < J1; k0 += nb) {
       const int kb = (int)std::min<int64_t>(nb, J1 - k0);
       double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
-      k_potrf_diag<<<1, DIAG_THREADS, sm, st>>>(B, ldb, k0, kb, nb, Uinv_k, w.flag);
-      count_launch();
+      // U_kk (one CTA), then U_kk^-1 (one warp per column, many SMs)
+      k_potrf_diag<<<1, DIAG_THREADS, sm, st>>>(B, ldb, k0, kb, nb, w.rdiag, w.flag);
+      k_trtri_cols<<<dim3((unsigned)ceil_div(nb, INV_WARPS), 1), INV_WARPS * 32, sm, st>>>(n, B, ldb, k0, nb, w.rdiag,
+                                                                                         Uinv_k, w.flag);
+      count_launch(2);
       GS_CHECK_LAUNCH();
       const int64_t rest = n - k0 - kb;
       if (rest <= 0) break;

@@ -170,10 +170,11 @@ int factor_ws(gsyeig_handle h, int64_t n, int nb, int64_t s, FactorWork &w) {
   const int64_t nblk = ceil_div(n, nb);
   GS_TRY(h->uinv.ensure((size_t)nblk * nb * nb * sizeof(double)));
   GS_TRY(h->panel.ensure((size_t)std::max<int64_t>(n, s) * nb * sizeof(double) + 64));
-  GS_TRY(h->flag.ensure(64));
+  GS_TRY(h->flag.ensure(256 + 160 * sizeof(double)));
   w.Uinv = h->uinv.d();
   w.panel = h->panel.d();
   w.flag = static_cast<int *>(h->flag.p);
+  w.rdiag = reinterpret_cast<double *>(static_cast<char *>(h->flag.p) + 256);
   return GSYEIG_SUCCESS;
 }
 
