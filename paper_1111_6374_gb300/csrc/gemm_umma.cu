@@ -13,9 +13,11 @@
 //  * Persistent CTAs (one per SM) walk the 128 x 64 tiles of C with
 //    warp-specialised roles: a producer lane, an MMA lane and 16 epilogue
 //    warps.  One thread issues tcgen05.mma.kind::f16 (bf16 x bf16 -> fp32,
-//    M = 128, N = 64, K = 16); the accumulator of level d lives in TMEM
-//    columns [64 d, 64 d + 64) (7 levels, 448 columns, 512 allocated).  Each
-//    K stage is 2 x 28 MMAs; tcgen05.commit releases the stage buffer.
+//    M = 128, K = 16); the accumulator of level d lives in TMEM columns
+//    [64 d, 64 d + 64) (7 levels, 448 columns, 512 allocated).  The 28 digit
+//    products of a k16 block go out as 10 MMAs of N = 64..256 (a run of B
+//    slices against one A slice fills a run of levels); tcgen05.commit
+//    releases the stage buffer.
 //  * K up to 512 per call, in exact chunks of K = 128: after each chunk the
 //    epilogue (warp w reads TMEM lane quarter w % 4, a quarter of the
 //    columns each) reads the 7 level sums with tcgen05.ld, recombines them
@@ -101,9 +103,25 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// instruction descriptor: kind::f16, bf16 A/B, fp32 D, K-major A/B, M = 128, N = 64
-__host__ __device__ constexpr uint32_t instr_desc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(UN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+// instruction descriptor: kind::f16, bf16 A/B, fp32 D, K-major A/B, M = 128, N = n
+__host__ __device__ constexpr uint32_t instr_desc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+}
+
+// The 28 digit products (p, q), p + q <= 6, as 10 MMAs: B slices q0..q0+nq-1
+// lie back to back in shared memory (one 64-row block each) and level d's
+// accumulator is TMEM columns [64 d, 64 d + 64), so A_p times the
+// (64 nq)-row block of those slices (N = 64 nq <= 256) writes levels
+// p + q0 .. p + q0 + nq - 1 in one instruction.  The two MMAs of p = 0
+// cover every level once: they start a chunk's accumulators.
+struct MmaGroup {
+  int p, q0, nq;
+};
+__host__ __device__ constexpr MmaGroup mma_group(int i) {
+  return i == 0 ? MmaGroup{0, 0, 4} : i == 1 ? MmaGroup{0, 4, 3} : i == 2 ? MmaGroup{1, 0, 4}
+       : i == 3 ? MmaGroup{1, 4, 2} : i == 4 ? MmaGroup{2, 0, 4} : i == 5 ? MmaGroup{2, 4, 1}
+       : i == 6 ? MmaGroup{3, 0, 4} : i == 7 ? MmaGroup{4, 0, 3} : i == 8 ? MmaGroup{5, 0, 2}
+                : MmaGroup{6, 0, 1};
 }
 
 __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
@@ -326,7 +344,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     }
   } else if (warp == MMA_WARP) {
     if (lane == 0) {
-      const uint32_t idesc = instr_desc();
+      const uint32_t idesc[5] = {0u, instr_desc(UN), instr_desc(2 * UN), instr_desc(3 * UN), instr_desc(4 * UN)};
       int64_t it = 0;
       int64_t fc = 0;  // chunks handed to the epilogue
       bool ok = true;
@@ -353,15 +371,12 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
 #pragma unroll
           for (int kb2 = 0; kb2 < KB2; kb2++)
 #pragma unroll
-            for (int q = 0; q < S; q++) {
-              const uint64_t bd = smem_desc(b0 + (uint32_t)((kb2 * S + q) * B_K16_BYTES), 128, 256);
-#pragma unroll
-              for (int p = 0; p < S - q; p++) {
-                const uint64_t ad = smem_desc(a0 + (uint32_t)((kb2 * S + p) * A_K16_BYTES), 128, 256);
-                // level d = p + q is first written at (kb2, q) = (0, 0) of a chunk's first stage
-                const uint32_t acc = (first && kb2 == 0 && q == 0) ? 0u : 1u;
-                umma(tmem + (uint32_t)((p + q) * UN), ad, bd, idesc, acc);
-              }
+            for (int gq = 0; gq < 10; gq++) {
+              const MmaGroup gr = mma_group(gq);
+              const uint64_t ad = smem_desc(a0 + (uint32_t)((kb2 * S + gr.p) * A_K16_BYTES), 128, 256);
+              const uint64_t bd = smem_desc(b0 + (uint32_t)((kb2 * S + gr.q0) * B_K16_BYTES), 128, 256);
+              const uint32_t acc = (first && kb2 == 0 && gr.p == 0) ? 0u : 1u;
+              umma(tmem + (uint32_t)((gr.p + gr.q0) * UN), ad, bd, idesc[gr.nq], acc);
             }
           umma_commit(&empty[b]);
           if ((ks % CH_STAGES) == CH_STAGES - 1 || ks == nks - 1) {
