@@ -245,7 +245,6 @@ constexpr int EPI_WARPS = 16;
 constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
 constexpr int UMMA_THREADS = (EPI_WARPS + 2) * 32;
 constexpr int EPI_COLS = UN / (EPI_WARPS / 4);  // columns of a tile per epilogue warp (16)
-constexpr int UPD = 2;  // elements a thread updates together
 
 // Exact integer value of a level sum (an integer-valued fp32, |x| < 2^24).
 __device__ __forceinline__ int32_t lvl(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
@@ -455,49 +454,53 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
       if (!ok) break;
       const bool row_ok = gi < g.M;  // (no early exit: the warp shuffles below need every lane)
       const int er = er_pre;
+      // which of this thread's 16 elements it writes (bit c), and their column exponents
+      uint32_t okm = 0;
+      int ecv[EPI_COLS];
 #pragma unroll
-      for (int c0 = 0; c0 < EPI_COLS; c0 += UPD) {
-        // gather first (independent loads in flight together), then convert, then store
-        bool ok[UPD];
-        int ecv[UPD];
-        double cold[UPD];
+      for (int c = 0; c < EPI_COLS; c++) {
+        const int64_t gj = gjb + c, dd = gi - gj + g.diag;
+        const bool ok = row_ok && (gj < g.N) && !(g.mode == TRI_LOWER && dd < 0) && !(g.mode == TRI_UPPER && dd > 0);
+        const int ecs = __shfl_sync(0xffffffffu, ec_pre, c);
+        ecv[c] = ok ? ecs : EXP_NONE;
+        okm |= ok ? (1u << c) : 0u;
+      }
+      if (alpha_pow2 && beta_mode != 2) {
+        // the solver's updates, C = +-2^k A B (+ C): V rounded to FP64 first
+        // (branch-free; the 128-bit accumulators die here), then every load
+        // of C in one burst (a store may alias a later load, so the compiler
+        // would not hoist them), then one FP64 add per element
+        double val[EPI_COLS];
 #pragma unroll
-        for (int c = 0; c < UPD; c++) {
-          const int64_t gj = gjb + c0 + c;
-          const int64_t dd = gi - gj + g.diag;
-          ok[c] = row_ok && (gj < g.N) && !(g.mode == TRI_LOWER && dd < 0) && !(g.mode == TRI_UPPER && dd > 0);
-          const int ecs = __shfl_sync(0xffffffffu, ec_pre, c0 + c);
-          ecv[c] = ok[c] ? ecs : EXP_NONE;
-          cold[c] = (ok[c] && beta_mode != 0) ? C[gi + gj * ldc] : 0.0;
+        for (int c = 0; c < EPI_COLS; c++) {
+          const bool live = (er != EXP_NONE && ecv[c] != EXP_NONE);
+          bool slow;
+          val[c] = i128_to_double(live ? vh[c] : 0, live ? vl[c] : 0ull, er + ecv[c] - 64 + ea2, neg_alpha, slow);
+          if (slow) val[c] = i128_ldexp(vh[c], vl[c], er + ecv[c] - 64 + ea2, neg_alpha);
         }
-        if (alpha_pow2 && beta_mode != 2) {
-          // the solver's updates: C = +-2^k A B (+ C): V rounded to FP64
-          // (branch-free), then one FP64 add
-          double val[UPD];
-          bool slow[UPD];
+        if (beta_mode == 1) {
+          double cold[EPI_COLS];
 #pragma unroll
-          for (int c = 0; c < UPD; c++) {
-            const bool live = (er != EXP_NONE && ecv[c] != EXP_NONE);
-            val[c] = i128_to_double(live ? vh[c0 + c] : 0, live ? vl[c0 + c] : 0ull, er + ecv[c] - 64 + ea2,
-                                    neg_alpha, slow[c]);
-          }
+          for (int c = 0; c < EPI_COLS; c++) cold[c] = ((okm >> c) & 1) ? C[gi + (gjb + c) * ldc] : 0.0;
 #pragma unroll
-          for (int c = 0; c < UPD; c++) {
-            if (!ok[c]) continue;
-            if (slow[c]) val[c] = i128_ldexp(vh[c0 + c], vl[c0 + c], er + ecv[c] - 64 + ea2, neg_alpha);
-            C[gi + (gjb + c0 + c) * ldc] = (beta_mode == 0) ? val[c] : cold[c] + val[c];
-          }
+          for (int c = 0; c < EPI_COLS; c++)
+            if ((okm >> c) & 1) C[gi + (gjb + c) * ldc] = cold[c] + val[c];
         } else {
 #pragma unroll
-          for (int c = 0; c < UPD; c++) {
-            if (!ok[c]) continue;
-            const int ec = ecv[c];
-            double ab = 0.0;
-            if (er != EXP_NONE && ec != EXP_NONE)
-              ab = alpha_pow2 ? i128_ldexp(vh[c0 + c], vl[c0 + c], er + ec - 64 + ea2, neg_alpha)
-                              : scale_slow(alpha, i128_ldexp(vh[c0 + c], vl[c0 + c], er + ec - 64, false));
-            C[gi + (gjb + c0 + c) * ldc] = (beta_mode == 0) ? ab : (beta_mode == 1 ? cold[c] + ab : fma(beta, cold[c], ab));
-          }
+          for (int c = 0; c < EPI_COLS; c++)
+            if ((okm >> c) & 1) C[gi + (gjb + c) * ldc] = val[c];
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < EPI_COLS; c++) {
+          if (!((okm >> c) & 1)) continue;
+          const int ec = ecv[c];
+          double ab = 0.0;
+          if (er != EXP_NONE && ec != EXP_NONE)
+            ab = alpha_pow2 ? i128_ldexp(vh[c], vl[c], er + ec - 64 + ea2, neg_alpha)
+                            : scale_slow(alpha, i128_ldexp(vh[c], vl[c], er + ec - 64, false));
+          const double cold = (beta_mode != 0) ? C[gi + (gjb + c) * ldc] : 0.0;
+          C[gi + (gjb + c) * ldc] = (beta_mode == 0) ? ab : (beta_mode == 1 ? cold + ab : fma(beta, cold, ab));
         }
       }
     }
