@@ -14,7 +14,10 @@
 // used twice (C_ij w_j and C_ij^T w_i): the kernel is HBM-bound.
 //
 // Layout: tile t = bi (bi + 1) / 2 + bj for bi >= bj; within a tile,
-// element (r, c) at r + 64 c (column-major); hi and lo in two arrays.
+// element (r, c) at (r ^ (c & 31)) + 64 c (column-major with the row index
+// XOR-swizzled by the column, so that a warp reading 32 rows of one column
+// and a warp reading one row of 32 columns both touch 32 distinct shared
+// memory banks); hi and lo in two arrays.
 // Diagonal tiles hold the full symmetric 64 x 64 block.  Partials go to
 // W[slot][row]: tile (bi, bj) writes its row sums to slot bj of rows in
 // block bi and (off-diagonal) its column sums to slot bi of rows in block
@@ -59,8 +62,9 @@ __global__ void k_op_build(int64_t n, int64_t NT, const double *__restrict__ C, 
     double v = 0.0;
     if (i < n && j < n) v = C[i + j * ldc];
     const float vh = (float)v;
-    h[idx] = vh;
-    l[idx] = (float)(v - (double)vh);
+    const int pos = (r ^ (c & 31)) + TS * c;
+    h[pos] = vh;
+    l[pos] = (float)(v - (double)vh);
   }
 }
 
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)NSTAGE * 2 * TILE_BYTES);
   __shared__ float2 xr[TS], xc[TS];  // w of the tile's column block (row sums), row block (col sums)
   __shared__ float2 rowp[4][TS];     // row-sum partials of the 4 column groups
-  __shared__ float2 colp[2][TS];     // column-sum partials of the 2 row halves
+  __shared__ float2 colp[4][TS];     // column-sum partials of the 4 row groups
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = lane + 32 * (warp & 1), g = warp >> 1;  // row, column group (16 columns)
@@ -169,12 +173,13 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
     if (s_fail) break;
     const float *h = sh + (size_t)(b * 2) * TS * TS, *l = h + TS * TS;
     float ch[16], cl[16];
+    // row sums: thread (row r, column group g) over columns 16 g .. 16 g + 15
 #pragma unroll
     for (int k = 0; k < 16; k++) {
-      ch[k] = h[r + TS * (g * 16 + k)];
-      cl[k] = l[r + TS * (g * 16 + k)];
+      const int col = g * 16 + k, pos = (r ^ (col & 31)) + TS * col;
+      ch[k] = h[pos];
+      cl[k] = l[pos];
     }
-    // row sums over this thread's 16 columns (compensated dot product)
     float rs = 0.f, rc = 0.f;
 #pragma unroll
     for (int k = 0; k < 16; k++) {
@@ -187,35 +192,26 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
     }
     rowp[g][r] = make_float2(rs, rc);
     if (!diag) {
-      // column sums: products c_rk * w_r, reduced over the 32 lanes by
-      // recursive halving (lane l ends up owning column g*16 + (l >> 1))
-      const float2 xi = xc[r];
-      float2 v[16];
+      // column sums (C_ij^T w_i): thread (column c = r, row group g) over
+      // rows 16 g .. 16 g + 15, read across the swizzle without conflicts
+      const int c = r;
 #pragma unroll
       for (int k = 0; k < 16; k++) {
+        const int row = g * 16 + k, pos = (row ^ (c & 31)) + TS * c;
+        ch[k] = h[pos];
+        cl[k] = l[pos];
+      }
+      float cs = 0.f, cc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const float2 x = xc[g * 16 + k];
         float p, e;
-        two_prod(ch[k], xi.x, p, e);
-        e = fmaf(ch[k], xi.y, e);
-        e = fmaf(cl[k], xi.x, e);
-        v[k] = make_float2(p, e);
+        two_prod(ch[k], x.x, p, e);
+        e = fmaf(ch[k], x.y, e);
+        e = fmaf(cl[k], x.x, e);
+        acc2(cs, cc, p, e);
       }
-#pragma unroll
-      for (int half = 8, o = 16; half >= 1; half >>= 1, o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int k = 0; k < half; k++) {
-          const float2 keep = up ? v[k + half] : v[k];
-          const float2 give = up ? v[k] : v[k + half];
-          float2 got;
-          got.x = __shfl_xor_sync(0xffffffffu, give.x, o);
-          got.y = __shfl_xor_sync(0xffffffffu, give.y, o);
-          v[k] = df_add(keep, got);
-        }
-      }
-      float2 other;
-      other.x = __shfl_xor_sync(0xffffffffu, v[0].x, 1);
-      other.y = __shfl_xor_sync(0xffffffffu, v[0].y, 1);
-      if ((lane & 1) == 0) colp[warp & 1][g * 16 + (lane >> 1)] = df_add(v[0], other);
+      colp[g][c] = make_float2(cs, cc);
     }
     __syncthreads();  // stage b fully read; partials complete
     if (threadIdx.x == 0 && issued < mine) {
@@ -229,7 +225,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
       W[(int64_t)bj * npad + (int64_t)bi * TS + rr] = a;
     } else if (!diag && threadIdx.x < 2 * TS) {
       const int cc = threadIdx.x - TS;
-      W[(int64_t)bi * npad + (int64_t)bj * TS + cc] = df_add(colp[0][cc], colp[1][cc]);
+      W[(int64_t)bi * npad + (int64_t)bj * TS + cc] = df_add(df_add(colp[0][cc], colp[1][cc]), df_add(colp[2][cc], colp[3][cc]));
     }
     __syncthreads();
   }
