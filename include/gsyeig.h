@@ -67,8 +67,9 @@ typedef struct {
   int32_t block;        /* panel width nb of the blocked factorisations, 16..160; 0 = default (128) */
   int32_t profile;      /* 1 = time every GEMM-engine and symv launch with CUDA events on the
                            library stream and report them in gsyeig_info (small overhead) */
-  int32_t fp64_gemm;    /* 0 (default): the O(n^3) GEMMs of gs1/gs2/bt1 with K <= 128 run on the bf16
-                           tensor cores (tcgen05) by error-free slicing (FP64-accurate, normwise);
+  int32_t fp64_gemm;    /* 0 (default): the GEMMs of gsyeig_solve (the O(n^3) ones of gs1/gs2/bt1 and the
+                           Lanczos basis products) run on the bf16 tensor cores (tcgen05) by
+                           error-free slicing (FP64-accurate, normwise), K in slabs of up to 512;
                            1: plain FP64 FMA; 2: the same slicing on the legacy mma.sync path */
   int32_t fp64_symv;    /* 0 (default): ke1 streams C's lower triangle as fp32 hi/lo tiles built once per
                            solve (C_hi + C_lo = C to ~2^-48) with compensated fp32 products, HBM-bound;

@@ -100,8 +100,10 @@ int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64
           TriMode mode = TRI_ALL, int64_t diag = 0, const int *abort_flag = nullptr);
 
 // How dgemm executes, installed per API call: sliced = true routes every
-// call with 1 <= K <= 128 to the error-free bf16 tensor-core GEMM
-// (gemm_sliced.cu) using the workspace ws; otherwise the FP64 FMA kernel.
+// call to the error-free bf16 tensor-core GEMM, in slabs of K (tcgen05
+// engine gemm_umma.cu: up to 512, exact chunks of 128 inside; mma.sync
+// engine gemm_sliced.cu: 128) using the workspace ws; otherwise the FP64
+// FMA kernel.
 struct GemmContext {
   bool sliced = false;
   bool umma = true;     // tcgen05 engine (else mma.sync engine)

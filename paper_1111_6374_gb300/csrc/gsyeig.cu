@@ -611,7 +611,7 @@ int gsyeig_syev_lanczos(gsyeig_handle h, const double *dC, int64_t ldc, int64_t 
   GS_TRY(begin(h));
   ProfScope prof(h);
   GemmScope gscope;
-  current_gemm() = nullptr;  // the Lanczos stage's GEMMs have K = m > 128: FP64 engine
+  current_gemm() = nullptr;  // no slicing workspace here: the basis products use the FP64 engine
   GS_TRY(h->hw.ensure((size_t)s * sizeof(double)));
   double ms_ke3 = 0;
   cudaEventRecord(h->ev[0], h->st);
