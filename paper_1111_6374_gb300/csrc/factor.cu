@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(double *B, int64_t 
                                                              double *rdiag, int *flag) {
   extern __shared__ double smem[];
   double *v = smem + (size_t)(nb + 1) * nb;  // scaled pivot row A(j, c) / A(j, j)
+  double *u = v + nb;                         // unscaled pivot row A(j, r)
   if (*flag) return;
   SmemBlock S{smem, nb + 1};
   const int t = threadIdx.x;
@@ -62,12 +63,18 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(double *B, int64_t 
       break;
     }
     const int w = kb - j - 1;
-    if (t < w) v[t] = S(j, j + 1 + t) * recip(d);
+    if (t < w) {
+      const double a = S(j, j + 1 + t);
+      u[t] = a;
+      v[t] = a * recip(d);
+    }
     __syncthreads();
-    // trailing update of the upper triangle: A(r, c) -= A(j, r) v(c), j < r <= c
-    for (int idx = t; idx < w * w; idx += blockDim.x) {
-      const int r = idx % w, c = idx / w;
-      if (r <= c) S(j + 1 + r, j + 1 + c) = fma(-S(j, j + 1 + r), v[c], S(j + 1 + r, j + 1 + c));
+    // trailing update of the upper triangle, A(r, c) -= A(j, r) v(c) for
+    // j < r <= c: a warp per column, lanes down its rows, so no lane of the
+    // (narrow, per-lane) FP64 pipe idles on the lower triangle
+    for (int c = t >> 5; c < w; c += DIAG_THREADS / 32) {
+      const double vc = v[c];
+      for (int r = t & 31; r <= c; r += 32) S(j + 1 + r, j + 1 + c) = fma(-u[r], vc, S(j + 1 + r, j + 1 + c));
     }
     __syncthreads();
   }
@@ -148,8 +155,8 @@ __global__ void __launch_bounds__(INV_WARPS * 32) k_trtri_cols(int64_t n, const 
   }
 }
 
-// shared memory of both diagonal-block kernels: the block plus one row
-size_t diag_smem_bytes(int nb) { return (size_t)(nb + 2) * nb * sizeof(double); }
+// shared memory of both diagonal-block kernels: the block plus two rows
+size_t diag_smem_bytes(int nb) { return (size_t)(nb + 3) * nb * sizeof(double); }
 
 int set_smem(const void *fn, size_t bytes) {
   if (bytes > 48 * 1024) GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
