@@ -73,3 +73,31 @@ def test_colmajor_helpers_cpu():
     T = torch.arange(12, dtype=torch.float64).reshape(4, 3)
     C = colmajor(T)
     assert C.stride(0) == 1 and torch.equal(C, T)
+
+
+@pytest.mark.parametrize("struct", ["gsyeig_opts", "gsyeig_info"])
+def test_binding_structs_match_the_header_layout(struct, tmp_path):
+    """The ctypes mirrors of gsyeig_opts / gsyeig_info have the header's
+    size and field offsets (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+
+    from paper_1111_6374_gb300 import Info, Opts
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    py = {"gsyeig_opts": Opts, "gsyeig_info": Info}[struct]
+    fields = [f for f, _ in py._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gsyeig.h"\nint main(void) {\n'
+                   f'  printf("size %zu\\n", sizeof({struct}));\n'
+                   + "".join(f'  printf("{f} %zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    assert int(got["size"]) == ctypes.sizeof(py)
+    for f in fields:
+        assert int(got[f]) == getattr(py, f).offset, f
