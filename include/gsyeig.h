@@ -85,6 +85,11 @@ typedef struct {
                            the matrix factored and B the one transformed.  If A's Cholesky meets a
                            non-positive pivot, A is restored and the direct route runs.  Ignored for
                            which = LARGEST. */
+  int32_t preserve_inputs; /* 1: device A and B are left as they were (the solve runs on copies held by
+                           the handle, 2 n^2 doubles); host inputs are never modified */
+  int32_t verify;       /* 1: after the solve, check the result against the original pencil in FP64
+                           on the device and report info.max_eta and info.orth_err (two more n^2
+                           copies; not part of the stage times) */
 } gsyeig_opts;
 
 /* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
@@ -109,6 +114,10 @@ typedef struct {
    * normalisation, restarts (QR iteration on T_m and V_m Q), Ritz problems on T_m */
   double orth_ms, restart_ms, ritz_ms;
   int64_t inverse;      /* 1 when the inverse problem (opts.inverse) was solved, else 0 */
+  /* opts.verify = 1: max over the pairs of the normwise backward error
+   * ||A x - lambda B x|| / ((||A|| + |lambda| ||B||) ||x||) (2-norms, the matrix norms by power
+   * iteration) and max |X^T B X - I|, both in FP64 against the original A and B; else 0 */
+  double max_eta, orth_err;
 } gsyeig_info;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t

@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("max_restarts", ctypes.c_int64), ("seed", ctypes.c_uint64), ("v0", ctypes.c_void_p),
                 ("timeout_ms", ctypes.c_double), ("block", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("fp64_gemm", ctypes.c_int32), ("fp64_symv", ctypes.c_int32),
-                ("qr_restart", ctypes.c_int32), ("inverse", ctypes.c_int32)]
+                ("qr_restart", ctypes.c_int32), ("inverse", ctypes.c_int32),
+                ("preserve_inputs", ctypes.c_int32), ("verify", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -50,7 +51,8 @@ class Info(ctypes.Structure):
                [(f, ctypes.c_int64) for f in ("gemm_launches", "symv_launches")] + \
                [(f, ctypes.c_double) for f in ("gemm_ms", "gemm_flops", "gemm_bytes", "symv_ms", "symv_flops",
                                                 "symv_bytes", "orth_ms", "restart_ms", "ritz_ms")] + \
-               [("inverse", ctypes.c_int64)]
+               [("inverse", ctypes.c_int64)] + \
+               [(f, ctypes.c_double) for f in ("max_eta", "orth_err")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -154,4 +154,11 @@ int trsm_back_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu, 
 // ---------------------------------------------------------------------------
 int symv_f64(cudaStream_t st, int64_t n, const double *C, int64_t ldc, const double *w, double *z);
 
+// verify.cu: max normwise backward error and max |X^T B X - I| of a solve's
+// pairs (w device, X device, ld ldx) against the full symmetric A0, B0, into
+// out[0], out[1] (host); ws holds verify_workspace_doubles(n, s) doubles.
+size_t verify_workspace_doubles(int64_t n, int64_t s);
+int verify_solution(cudaStream_t st, int64_t n, int64_t s, const double *A0, int64_t lda, const double *B0,
+                    int64_t ldb, const double *X, int64_t ldx, const double *w, double *ws, double out[2]);
+
 }  // namespace gs

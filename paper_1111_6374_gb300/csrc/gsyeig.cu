@@ -52,6 +52,8 @@ struct gsyeig_ctx {
   DevBuf uinv, panel, flag, diag;
   DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts, arrow;
   DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
+  DevBuf pA, pB;          // working copies when opts.preserve_inputs
+  DevBuf vA, vB, vws;     // originals and workspace of opts.verify
   DevBuf gemm_ws;         // slices of the tensor-core GEMM
   DevBuf gemm_err;        // device error flag of the tcgen05 engine
   DevBuf dfop, dfpart;    // double-float operator tiles and symv partials
@@ -464,7 +466,7 @@ int gsyeig_destroy(gsyeig_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
-  DevBuf *bufs[] = {&h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
+  DevBuf *bufs[] = {&h->pA, &h->pB, &h->vA, &h->vB, &h->vws, &h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
                     &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
                     &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
   for (DevBuf *b : bufs) b->release();
@@ -482,7 +484,8 @@ int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
   if (!(o->tol > 0.0) || o->krylov_dim < 0 || o->keep < 0 || o->max_restarts < 0 || o->timeout_ms < 0 ||
       o->block < 0 || o->block > 160 || (o->block > 0 && o->block < 16) || o->profile < 0 || o->profile > 1 ||
       o->fp64_gemm < 0 || o->fp64_gemm > 2 || o->fp64_symv < 0 || o->fp64_symv > 1 || o->qr_restart < 0 ||
-      o->qr_restart > 1 || o->inverse < 0 || o->inverse > 1)
+      o->qr_restart > 1 || o->inverse < 0 || o->inverse > 1 || o->preserve_inputs < 0 ||
+      o->preserve_inputs > 1 || o->verify < 0 || o->verify > 1)
     return -2;
   if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
   h->opts = *o;
@@ -664,6 +667,28 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     GS_CUDA(cudaMemcpy2DAsync(dB, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), n,
                               cudaMemcpyHostToDevice, st));
   }
+  if (!hostA && h->opts.preserve_inputs == 1) {  // solve on copies; the caller's A, B stay as they were
+    GS_TRY(h->pA.ensure((size_t)n * n * sizeof(double)));
+    GS_TRY(h->pB.ensure((size_t)n * n * sizeof(double)));
+    GS_CUDA(cudaMemcpy2DAsync(h->pA.p, n * sizeof(double), A, lda * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemcpy2DAsync(h->pB.p, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, st));
+    dA = h->pA.d();
+    dB = h->pB.d();
+    dlda = dldb = n;
+  }
+  const bool verify = h->opts.verify == 1;
+  if (verify) {  // the originals, completed from the triangles the route reads (A lower, B upper)
+    GS_TRY(h->vA.ensure((size_t)n * n * sizeof(double)));
+    GS_TRY(h->vB.ensure((size_t)n * n * sizeof(double)));
+    GS_CUDA(cudaMemcpy2DAsync(h->vA.p, n * sizeof(double), dA, dlda * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, st));
+    GS_CUDA(cudaMemcpy2DAsync(h->vB.p, n * sizeof(double), dB, dldb * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, st));
+    GS_TRY(symmetrize(st, n, h->vA.d(), n, true));
+    GS_TRY(symmetrize(st, n, h->vB.d(), n, false));
+  }
   const int nb = nb_of(h, n);
   FactorWork fw;
   GS_TRY(factor_ws(h, n, nb, s, fw));
@@ -740,6 +765,16 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   GS_TRY(finish(h));
   GS_TRY(gemm_check(h));
   prof.fill(info);
+  if (verify) {  // after the end mark: not part of the stage times
+    double vout[2] = {0.0, 0.0};
+    GS_TRY(h->vws.ensure(verify_workspace_doubles(n, s) * sizeof(double)));
+    GS_TRY(verify_solution(st, n, s, h->vA.d(), n, h->vB.d(), n, dX, dldx, h->hw.d(), h->vws.d(), vout));
+    GS_TRY(gemm_check(h));
+    if (info) {
+      info->max_eta = vout[0];
+      info->orth_err = vout[1];
+    }
+  }
   if (info) {
     info->ms_gs1 = elapsed(h->ev[1], h->ev[2]);
     info->ms_gs2 = elapsed(h->ev[2], h->ev[3]);

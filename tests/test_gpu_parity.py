@@ -194,6 +194,37 @@ def test_solve_inverse_falls_back_to_direct_route():
         _check_pairs(A, B, _np(w), _np(X), w_or, lam, f"fallback {which}")
 
 
+@pytest.mark.parametrize("inverse", [0, 1], ids=["direct", "inverse"])
+def test_solve_preserve_inputs_and_verify(inverse):
+    """opts.preserve_inputs leaves device A and B bit for bit as they were;
+    opts.verify reports the normwise backward error and B-orthonormality of
+    the returned pairs, computed on the device against the original pencil,
+    in agreement with the host checker (norms by power iteration on both
+    sides, so within a factor 2 for eta)."""
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = 512, 10
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=31))
+    w_or, _ = oracle.gsyeig(A, B, s)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    A0, B0 = dA.clone(), dB.clone()
+    sol = Solver(0, preserve_inputs=1, verify=1, inverse=inverse)
+    w, X, info = sol.solve(dA, dB, s, overwrite=True)
+    assert torch.equal(dA, A0) and torch.equal(dB, B0)
+    assert info["inverse"] == inverse
+    w, X = _np(w), _np(X)
+    _check_pairs(A, B, w, X, w_or, lam, f"preserve inverse={inverse}")
+    et = float(_checks.eta(A, B, w, X).max())
+    assert 0.0 < info["max_eta"] <= 1e-10
+    assert 0.5 * et <= info["max_eta"] <= 2.0 * et, (info["max_eta"], et)
+    ob = _checks.b_orth_err(B, X)
+    assert info["orth_err"] <= 1e-10 and abs(info["orth_err"] - ob) <= 1e-13, (info["orth_err"], ob)
+    # host pointers: the staged copies are verified the same way
+    w_h, X_h, info_h = sol.solve(torch.from_numpy(A), torch.from_numpy(B), s)
+    assert info_h["max_eta"] <= 1e-10 and info_h["orth_err"] <= 1e-10
+    assert abs(info_h["max_eta"] - info["max_eta"]) <= 1e-3 * info["max_eta"]
+
+
 def test_badly_scaled_factorisations(any_solver):
     """Rows/columns spanning 1e-6..1e6.  Both GEMM engines must be normwise
     backward stable (||U^T U - B|| / ||B||); the FP64 engine is also
