@@ -225,6 +225,22 @@ def test_solve_preserve_inputs_and_verify(inverse):
     assert abs(info_h["max_eta"] - info["max_eta"]) <= 1e-3 * info["max_eta"]
 
 
+@pytest.mark.parametrize("nb", [64, 96, 160])
+def test_solve_block_sizes(nb):
+    """Panel widths other than the default: rank-4nb trailing updates (K
+    slabs of the GEMM engine), ragged last blocks, and nb > 128 on the FP64
+    engine, all giving the oracle's pairs."""
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = 700, 8
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=nb))
+    w_or, _ = oracle.gsyeig(A, B, s)
+    for inverse in (0, 1):
+        w, X, info = Solver(0, block=nb, inverse=inverse).solve(torch.from_numpy(A).cuda(),
+                                                                 torch.from_numpy(B).cuda(), s)
+        _check_pairs(A, B, _np(w), _np(X), w_or, lam, f"nb={nb} inverse={inverse}")
+
+
 def test_badly_scaled_factorisations(any_solver):
     """Rows/columns spanning 1e-6..1e6.  Both GEMM engines must be normwise
     backward stable (||U^T U - B|| / ||B||); the FP64 engine is also
