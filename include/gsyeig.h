@@ -65,7 +65,7 @@ typedef struct {
   const double *v0;     /* optional device start vector of length n (NULL = random) */
   double timeout_ms;    /* 0 = none; checked between restarts only */
   int32_t block;        /* panel width nb of the blocked factorisations, 16..160; 0 = default (128).  The
-                           trailing matrix gets rank-4nb updates; nb > 128 runs the FP64 GEMM engine */
+                           trailing matrix gets rank-4nb updates */
   int32_t profile;      /* 1 = time every GEMM-engine and symv launch with CUDA events on the
                            library stream and report them in gsyeig_info (small overhead) */
   int32_t fp64_gemm;    /* 0 (default): the GEMMs of gsyeig_solve (the O(n^3) ones of gs1/gs2/bt1 and the

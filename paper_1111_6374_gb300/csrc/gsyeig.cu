@@ -134,7 +134,7 @@ int nb_of(gsyeig_handle h, int64_t n) {
 // operands of at most max(n, s) rows and K up to the outer block 4 nb (the
 // tcgen05 engine takes up to 512 per call).
 int gemm_setup(gsyeig_handle h, int64_t n, int nb, int64_t s) {
-  h->gemm.sliced = (h->opts.fp64_gemm != 1) && nb <= 128;
+  h->gemm.sliced = (h->opts.fp64_gemm != 1);
   h->gemm.umma = (h->opts.fp64_gemm == 0);
   if (h->gemm.sliced) {
     const int64_t r = std::max<int64_t>(n, s);

@@ -228,8 +228,8 @@ def test_solve_preserve_inputs_and_verify(inverse):
 @pytest.mark.parametrize("nb", [64, 96, 160])
 def test_solve_block_sizes(nb):
     """Panel widths other than the default: rank-4nb trailing updates (K
-    slabs of the GEMM engine), ragged last blocks, and nb > 128 on the FP64
-    engine, all giving the oracle's pairs."""
+    slabs of the GEMM engine, 640 = 512 + 128 at nb = 160) and ragged last
+    blocks, all giving the oracle's pairs."""
     from paper_1111_6374_gb300 import Solver
 
     n, s = 700, 8
