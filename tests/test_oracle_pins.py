@@ -189,6 +189,26 @@ def test_largest_and_smallest():
     assert np.max(np.abs(w - lam[:7]) / lam[:7]) < 1e-10
 
 
+def test_inverse_problem_relation():
+    """Section 3.1's inverse problem, as the GPU route's reading uses it: with
+    A and B positive definite, the s largest pairs (mu, y) of B y = mu A y
+    (y^T A y = 1) give the s smallest pairs of (A, B) as lambda = 1/mu in
+    reverse order and x = y / sqrt(mu) (then x^T B x = 1)."""
+    n, s = 400, 9
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, 12))
+    assert lam.min() > 0
+    mu, Y = oracle.gsyeig(B, A, s, which="largest")  # roles swapped: A is the SPD matrix factored
+    assert np.abs(Y.T @ A @ Y - np.eye(s)).max() < 1e-10
+    w_inv = 1.0 / mu[::-1]
+    X_inv = Y[:, ::-1] / np.sqrt(mu[::-1])
+    w, X = oracle.gsyeig(A, B, s)
+    assert np.max(np.abs(w_inv - w) / w) < 1e-10
+    assert np.max(np.abs(w_inv - lam[:s]) / lam[:s]) < 1e-10
+    assert np.abs(X_inv.T @ B @ X_inv - np.eye(s)).max() < 1e-10
+    # the same vectors up to sign (the constructed spectrum has no clusters at the bottom)
+    assert np.abs(np.abs(np.sum(X_inv * (B @ X), axis=0)) - 1.0).max() < 1e-8
+
+
 def test_standard_problem_special_case():
     n = 90
     A = _sym(n, 41)
