@@ -61,3 +61,21 @@ def test_max_over_ranks_gloo_world2():
         p.join(timeout=120)
         assert p.exitcode == 0
     assert out[0] == out[1] == 11.0
+
+
+def test_committed_traffic_matches_current_kernel_sources():
+    """profiles/traffic.json holds DRAM bytes only for kernel sources whose
+    hash it records; both captured kernels match the committed sources, and
+    the operator's figure scales with n^2 to the benchmark size."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sym = bench.kernel_traffic("k_symv_df", 6144)
+    gem = bench.kernel_traffic("k_sliced_umma", 16384)
+    assert sym is not None and gem is not None, "ncu capture is stale: re-profile the changed kernel"
+    sym16 = bench.kernel_traffic("k_symv_df", 16384)
+    assert abs(sym16["dram_bytes"] / sym["dram_bytes"] - (16384 / 6144) ** 2) < 1e-12
+    # algorithmic bytes of one symv at n = 6144 (triangle hi + lo, w and z); traffic within 10%
+    alg = 8.0 * 6144 * 6145 / 2 + 16.0 * 6144
+    assert 1.0 <= sym["dram_bytes"] / alg < 1.1
+    assert bench.kernel_traffic("no_such_kernel", 100) is None
