@@ -167,9 +167,30 @@ def kernel_traffic(kernel: str, n: int):
             "note": f"ncu capture at n={e['n']} ({e['dram_bytes_per_launch']:.4g} B), scaled by {e.get('scales_with', '1')}"}
 
 
+def oracle_exponent(n_full: int, n_sample: int):
+    """Growth exponent p of the oracle's time, t(n_full) = t(n_sample)
+    (n_full / n_sample)^p, fitted from the committed full-size timing
+    (profiles/cpu_oracle.json: one run at n_full and runs at n_sample on the
+    same host cores); p = 3 (every oracle stage is O(n^3)) if that record is
+    absent or for other sizes."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "cpu_oracle.json")) as f:
+            d = json.load(f)
+        if d["n_full"] == n_full and d["n_sample"] == n_sample:
+            import math
+
+            p = math.log(d["seconds_full"] / d["seconds_sample"]) / math.log(n_full / n_sample)
+            return p, (f"fitted from one oracle run at n={n_full} ({d['seconds_full']:.0f} s) and n={n_sample} "
+                       f"({d['seconds_sample']:.2f} s) on {d['cores']} cores (profiles/cpu_oracle.json)")
+    except (OSError, KeyError, ValueError, ZeroDivisionError):
+        pass
+    return 3.0, "assumed (every oracle stage is O(n^3)); no committed full-size timing for this size"
+
+
 def cpu_oracle_sample(n_full: int, s_full: int, n_sample: int):
     """Time the oracle on the leading n_sample x n_sample sub-pencil and
-    scale by (n_full / n_sample)^3 (every stage of the oracle is O(n^3))."""
+    scale by (n_full / n_sample)^p, p from oracle_exponent (the value is an
+    extrapolation and says so)."""
     import inputs
     import oracle
 
@@ -178,10 +199,12 @@ def cpu_oracle_sample(n_full: int, s_full: int, n_sample: int):
     t0 = time.perf_counter()
     oracle.gsyeig(A, B, s, vectors="invit")
     dt = time.perf_counter() - t0
-    scale = (n_full / n_sample) ** 3
+    p, how = oracle_exponent(n_full, n_sample)
+    scale = (n_full / n_sample) ** p
     return {"value": dt * scale, "unit": "s", "cores": oracle.num_threads(), "kind": "oracle",
+            "extrapolated": n_sample != n_full, "exponent": p, "exponent_source": how, "sample_seconds": dt,
             "sample": f"oracle on the leading {n_sample}x{n_sample} sub-pencil (s={s}), {dt:.2f} s measured, "
-                      f"scaled by (n/{n_sample})^3 = {scale:.0f}"}
+                      f"scaled by (n/{n_sample})^{p:.3f} = {scale:.1f}"}
 
 
 def run_reference(args, ws, rank):
@@ -194,12 +217,18 @@ def run_reference(args, ws, rank):
     for _ in range(args.steps):
         vals.append(cpu_oracle_sample(args.n, args.s, n_sample))
     v = statistics.mean(x["value"] for x in vals)
+    sample_ms = statistics.mean(x["sample_seconds"] for x in vals) * 1e3
+    # each timed step is one oracle run on the bounded sample: ms_per_step is
+    # that measured time; value is the time-to-solution at the configured n,
+    # extrapolated from it with the exponent stated
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": args.n, "s": args.s, "which": "smallest"},
+            "warmup": args.warmup, "ms_per_step": sample_ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "extrapolated": vals[0]["extrapolated"],
+            "config": {"workload": args.workload, "n": args.n, "s": args.s, "which": "smallest",
+                       "sample_n": n_sample},
             "cpu_baseline": {"value": v, "unit": "s", "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+                             "sample": vals[0]["sample"], "extrapolated": vals[0]["extrapolated"],
+                             "exponent": vals[0]["exponent"], "exponent_source": vals[0]["exponent_source"]},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -218,10 +247,13 @@ def run_ours(args, ws, rank, local):
     from paper_1111_6374_gb300 import Solver, kernel_launches
 
     n, s = args.n, args.s
-    A0, B0, lam = inputs.make_pencil(n, seed=args.seed + rank, device=dev)
+    if args.gen_device == "cpu":  # e.g. under a profiler that cannot load torch's CUDA linear algebra
+        A0, B0, lam = (t.to(dev) for t in inputs.make_pencil(n, seed=args.seed + rank))
+    else:
+        A0, B0, lam = inputs.make_pencil(n, seed=args.seed + rank, device=dev)
     A = torch.empty_like(A0)
     B = torch.empty_like(B0)
-    solver = Solver(local, inverse=1 if args.route == "inverse" else 0)
+    solver = Solver(local, inverse=1 if args.route == "inverse" else 0, block=args.block)
     stream = torch.cuda.current_stream(dev)
 
     def restore():
@@ -300,6 +332,25 @@ def run_ours(args, ws, rank, local):
                  "ms_orth": oi["orth_ms"]}
         osol.close()
 
+    def one_solve(**opts):
+        """One profiled solve of the benchmark pencil with other options (no warm-up)."""
+        sol = Solver(local, **opts)
+        _, _, t, i = timed(sol, 1, 0)
+        i = i[-1]
+        sol.close()
+        return {"ms_per_step": max_over_ranks(t[0], ws, dev), "steps": 1, "options": opts,
+                "inverse_used": i["inverse"], "matvecs": i["matvecs"], "restarts": i["restarts"],
+                "stages_ms": {k: i[k] for k in ("ms_gs1", "ms_gs2", "ms_ke", "ms_ke3", "ms_bt1", "ms_total")}}
+
+    # variant KI (C never formed, U^-1 applied by triangular products)
+    ki = None if args.no_extra else one_solve(inverse=1 if args.route == "inverse" else 0, implicit=1)
+    # the same route in plain FP64 arithmetic (FP64 FMA GEMMs and symv)
+    plain = None if args.no_extra else one_solve(inverse=1 if args.route == "inverse" else 0, fp64_gemm=1,
+                                                  fp64_symv=1)
+    # library comparison on the same GPU: cuSOLVER through torch.linalg
+    # (Cholesky, two triangular solves, a full symmetric eigensolver)
+    library = None if args.no_extra else _library_point(A0, B0, s, lam)
+
     if rank != 0:
         return 0
     peaks, src = load_peaks()
@@ -309,6 +360,9 @@ def run_ours(args, ws, rank, local):
     g_ms = sum(i["gemm_ms"] for i in infos) / nst
     g_fl = sum(i["gemm_flops"] for i in infos) / nst
     g_n = sum(i["gemm_launches"] for i in infos) / nst
+    c_ms = sum(i["gemm_core_ms"] for i in infos) / nst
+    c_fl = sum(i["gemm_core_flops"] for i in infos) / nst
+    c_n = sum(i["gemm_core_launches"] for i in infos) / nst
     s_ms = sum(i["symv_ms"] for i in infos) / nst
     s_fl = sum(i["symv_flops"] for i in infos) / nst
     s_by = sum(i["symv_bytes"] for i in infos) / nst
@@ -317,11 +371,22 @@ def run_ours(args, ws, rank, local):
     # GEMM engine of gs1/gs2/bt1: FP64-equivalent rate; on the tensor path the
     # algorithmic tensor work is 28 bf16 digit-pair products per FP64 product
     g_fp64eq = g_fl / (g_ms * 1e-3) / 1e12 if g_ms > 0 else 0.0
+    core = None
     if sliced:
-        gemm = {"kernel": "k_sliced_umma (+ slicing kernels): FP64-accurate GEMM of gs1/gs2/bt1 on tcgen05",
+        gemm = {"kernel": "GEMM engine calls (k_sliced_umma + the kernels slicing FP64 operands into bf16 digits)",
                 "bound": "tensor", "achieved": 28 * g_fp64eq, "peak": bf16, "unit": "TFLOP/s",
                 "frac": 28 * g_fp64eq / bf16, "fp64_equivalent_tflops": g_fp64eq,
                 "peak_source": f"{src} bf16 (MEASURED_PEAKS.json)"}
+        if c_ms > 0 and solver.opts.fp64_gemm == 0:
+            c_eq = c_fl / (c_ms * 1e-3) / 1e12
+            core = {"kernel": "k_sliced_umma: the tcgen05 kernel alone (28 bf16 digit products per FP64 product)",
+                    "bound": "tensor", "achieved": 28 * c_eq, "peak": bf16, "unit": "TFLOP/s",
+                    "frac": 28 * c_eq / bf16, "fp64_equivalent_tflops": c_eq,
+                    "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)",
+                    "launches_per_step": c_n, "ms_per_step": c_ms, "share_of_step": c_ms / ms,
+                    "ms_per_launch": c_ms / max(1.0, c_n),
+                    "algorithmic_flops_per_launch": 28 * c_fl / max(1.0, c_n),
+                    "slicing_ms_per_step": g_ms - c_ms}
     else:
         fp64_peak = bf16 * FP64_OVER_BF16_NOMINAL
         gemm = {"kernel": "k_dgemm: FP64 FMA GEMM of gs1/gs2/bt1", "bound": "alu", "achieved": g_fp64eq,
@@ -336,12 +401,16 @@ def run_ours(args, ws, rank, local):
             "algorithmic_bytes_per_launch": s_by / max(1, s_n), "launches_per_step": s_n,
             "ms_per_launch": s_ms / max(1, s_n), "fp64_equivalent_tflops": s_fl / (s_ms * 1e-3) / 1e12 if s_ms else 0.0,
             "share_of_step": s_ms / ms}
-    for k, name in ((gemm, "k_sliced_umma" if sliced else "k_dgemm"), (symv, "k_symv_df" if df else "k_symv_cols_v2")):
+    for k, name in ((core, "k_sliced_umma"), (symv, "k_symv_df" if df else "k_symv_cols_v2")):
+        if k is None:
+            continue
         tr = kernel_traffic(name, n)
         k["traffic"] = tr["dram_bytes"] if tr else None
         k["traffic_note"] = tr["note"] if tr else "no ncu capture of the current source"
-    roof = symv if symv["share_of_step"] >= gemm["share_of_step"] else gemm
+    dominant = core if core is not None else gemm
+    roof = symv if symv["share_of_step"] >= dominant["share_of_step"] else dominant
     last = infos[-1]
+    acc_ok = bool(rel <= 1e-10 and eta <= 1e-10 and orth <= 1e-10)
     line = {
         "metric": METRIC, "value": ms_all / 1e3, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": False, "scaling": "weak",
@@ -354,18 +423,65 @@ def run_ours(args, ws, rank, local):
         "lanczos": {"matvecs": last["matvecs"], "restarts": last["restarts"], "nconv": last["nconv"],
                     "ms_symv": last["symv_ms"], "ms_orth": last["orth_ms"], "ms_restart": last["restart_ms"],
                     "ms_ritz": last["ritz_ms"]},
+        # live per-class CUDA-event times of one step (the library stream, profile = 1)
+        "classes_ms_per_step": {"gemm_core (k_sliced_umma)": c_ms, "gemm_slicing": g_ms - c_ms,
+                                "diag_blocks (k_potrf_diag + k_trtri_cols)": sum(i["diag_ms"] for i in infos) / nst,
+                                "symv (ke1)": s_ms, "orth (CGS2 + normalise)": sum(i["orth_ms"] for i in infos) / nst,
+                                "ritz": sum(i["ritz_ms"] for i in infos) / nst,
+                                "restart": sum(i["restart_ms"] for i in infos) / nst},
         "accuracy": {"max_rel_eig_err_vs_constructed": rel, "max_eta": eta, "orth_err": orth},
-        "roofline": roof, "kernels": {"gemm": gemm, "symv": symv},
+        "accuracy_ok": acc_ok,
+        "roofline": roof, "kernels": {"gemm_core": core, "gemm_engine": gemm, "symv": symv},
         "e2e": ({"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": (n * s + s) * 8}
                 if e2e is not None else None),
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "other_route": other,
+        "variant_ki": ki,
+        "plain_fp64": plain,
+        "library_cusolver": library,
     }
     if args.gpus == 1 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(n, s, args.cpu_sample_n)
     print(json.dumps(line), flush=True)
-    return 0
+    # a time that does not meet the accuracy the metric is quoted at is not a result
+    return 0 if acc_ok else 3
+
+
+def _library_point(A0, B0, s, lam):
+    """cuSOLVER (torch.linalg) on the same pencil and GPU, for comparison
+    only: B = U^T U, C = U^-T A U^-1 by two triangular solves, all
+    eigenpairs of C (syevd), the s smallest back-transformed.  One timed run
+    after a small warm-up call."""
+    import torch
+
+    def run(A, B):
+        U = torch.linalg.cholesky(B, upper=True)
+        W = torch.linalg.solve_triangular(U.T, A, upper=False)
+        C = torch.linalg.solve_triangular(U.T, W.T, upper=False).T
+        del W
+        C = 0.5 * (C + C.T)
+        w, Y = torch.linalg.eigh(C)
+        X = torch.linalg.solve_triangular(U, Y[:, :s].contiguous(), upper=True)
+        return w[:s], X
+
+    try:
+        run(A0[:256, :256].clone(), B0[:256, :256].clone())  # library handles and workspaces
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        w, X = run(A0, B0)
+        e1.record()
+        torch.cuda.synchronize()
+        rel = float(((w - lam[:s]).abs() / lam[:s].abs()).max())
+        out = {"ms": e0.elapsed_time(e1), "what": "torch.linalg cholesky + 2 x solve_triangular + eigh (cuSOLVER "
+               "syevd, all n pairs) + solve_triangular, FP64", "max_rel_eig_err_vs_constructed": rel}
+        del w, X
+        torch.cuda.empty_cache()
+        return out
+    except RuntimeError as e:  # e.g. out of memory
+        return {"error": str(e).splitlines()[0][:200]}
 
 
 def _power(M, iters=30):
@@ -399,6 +515,11 @@ def main(argv=None):
                     help="inverse: largest eigenpairs of B X = A X Lambda^-1 (A is positive definite here); "
                          "direct: smallest of C = U^-T A U^-1")
     ap.add_argument("--no-other-route", action="store_true", help="skip the comparison run of the other route")
+    ap.add_argument("--gen-device", choices=["cuda", "cpu"], default="cuda",
+                    help="where the synthetic pencil is built (input generation only, outside any timing)")
+    ap.add_argument("--block", type=int, default=0, help="panel width nb of the blocked factorisations (0 = default)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the comparison solves (variant KI, plain FP64, cuSOLVER)")
     args = ap.parse_args(argv)
     args.workload = f"gsyeig n={args.n} s={args.s} smallest, FP64, known-spectrum synthetic pencil"
     ws, rank, local = dist_env()

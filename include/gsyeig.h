@@ -91,6 +91,41 @@ typedef struct {
   int32_t verify;       /* 1: after the solve, check the result against the original pencil in FP64
                            on the device and report info.max_eta and info.orth_err (two more n^2
                            copies; not part of the stage times) */
+  int32_t implicit;     /* 0 (default): variant KE, C = U^-T G U^-1 formed explicitly (gs2) and applied
+                           by ke1.  1: variant KI (Section 2.3, Table 1): C is never formed; each
+                           Lanczos step applies z = U^-T (G (U^-1 w)) with the untouched G (A, or B on
+                           the inverse route) and the triangular factor, 4n^2 flops per step.  The
+                           two triangular solves are applied through the explicit inverse U^-1,
+                           computed once after gs1 on the tensor-core engine (see gsyeig_solve).
+                           On exit G is left as it was (its lower triangle mirrored into the
+                           upper) instead of holding C. */
+  int32_t wait_limit;   /* testing hook, 0 (default) = off.  > 0: the device-side waits inside the main
+                           loops of the tensor-core GEMM and of the ke1 kernel give up after this many
+                           polls instead of after about a second, so that a test can make them run
+                           out and check that the call returns GSYEIG_TIMEOUT and that the next call
+                           with wait_limit = 0 succeeds.  Results of a call that timed out are
+                           invalid. */
+  /* Warm start for a sequence of related problems (the paper's Section 3 motivates it with the
+   * dozens of related problems of a DFT self-consistency cycle).  With start_block != NULL the
+   * Lanczos start vector is F (X0 w): X0 (n x start_cols, leading dimension ld_start, device) holds
+   * eigenvector approximations of the pencil (e.g. a previous solve's X), w (start_weights, device,
+   * start_cols entries; NULL = all ones) mixes them, and F is the upper-triangular factor of gs1
+   * that maps them into the operator's space.  start_block takes precedence over v0. */
+  const double *start_block;
+  const double *start_weights;
+  int64_t start_cols, ld_start;
+  /* filter_degree > 0: before the first Lanczos step the start vector goes through the Chebyshev
+   * polynomial of that degree (at most 64) that is bounded by 1 on the interval between
+   * filter_cut and filter_edge (the unwanted end of the operator's spectrum: [cut, edge] with
+   * edge above the cut for the smallest pairs, below it for the largest) and grows fast outside
+   * it (Zhou and Saad's Chebyshev filter); each degree costs one operator application, counted
+   * in info.matvecs and info.filter_matvecs. */
+  double filter_cut, filter_edge;
+  int32_t filter_degree;
+  /* check_every > 0: besides the end of every cycle, test the wanted Ritz pairs after every
+   * check_every Lanczos steps (once the projected matrix holds the kept pairs), so that a good
+   * start can stop before the Krylov dimension is reached; 0 (default): at the end of a cycle only. */
+  int32_t check_every;
 } gsyeig_opts;
 
 /* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
@@ -119,6 +154,18 @@ typedef struct {
    * ||A x - lambda B x|| / ((||A|| + |lambda| ||B||) ||x||) (2-norms, the matrix norms by power
    * iteration) and max |X^T B X - I|, both in FP64 against the original A and B; else 0 */
   double max_eta, orth_err;
+  /* opts.profile = 1: the tensor-core kernel of the GEMM engine alone (gemm_ms above also covers
+   * the kernels that slice the FP64 operands into bf16 digit planes), with the FP64-equivalent
+   * flops of those launches */
+  int64_t gemm_core_launches;
+  double gemm_core_ms, gemm_core_flops;
+  /* opts.profile = 1: the kernels that factor and invert the nb x nb diagonal blocks of gs1 (pairs of
+   * launches) and their summed event time */
+  int64_t diag_launches;
+  double diag_ms;
+  double tnorm;           /* the recurrence's running estimate of ||T|| (bounds the operator's spectrum
+                             from the Krylov space: a filter_edge for a following solve) */
+  int64_t filter_matvecs; /* operator applications of the start vector's Chebyshev filter */
 } gsyeig_info;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -141,8 +188,7 @@ const char *gsyeig_strerror(int status);
  * The whole KE route (Section 2.3) for the s smallest (which = SMALLEST) or
  * largest eigenpairs of (A, B), 1 <= s < n.
  *  dA (n x n, lda): on entry the symmetric A, lower triangle read; on exit
- *      C = U^-T A U^-1 stored full (Eq. 3: "the entries of A can be
- *      overwritten with the result C").
+ *      C = U^-T A U^-1 stored full, written over A (Section 2.1, Eq. 3).
  *  dB (n x n, ldb): on entry the SPD B, upper triangle read; on exit U in
  *      the upper triangle (Eq. 2); the strictly lower triangle is not touched.
  *  w  (s): eigenvalues in ascending order.  Host or device pointer.
@@ -204,9 +250,11 @@ int gsyeig_tridiag_eig(gsyeig_handle h, const double *d, const double *e, int64_
  * with dZ != NULL the call requires 5 * m * cnt <= 1048576 and otherwise
  * returns GSYEIG_SCRATCH_TOO_SMALL without touching the outputs.  Runs on
  * the calling thread's current device, on `cuda_stream` (cudaStream_t, NULL =
- * legacy default stream), synchronous on return.  The first call on a device
- * looks up the scratch address for that device; make that first call before
- * any stream capture.  All calls share the one scratch array: calls whose
+ * legacy default stream), synchronous on return.  The call looks up the
+ * scratch address on the current device (a lookup allocates nothing), so
+ * the address stays right after a device reset; the first call on a device
+ * does this set-up for that device: make it before any stream capture.
+ * All calls share the one scratch array: calls whose
  * work overlaps on the GPU (other streams, other host threads) race and must
  * be serialised by the caller.  Argument codes: -1 d, -2 e, -3 m, -4 first,
  * -5 cnt, -6 lam, -8 ldz. */

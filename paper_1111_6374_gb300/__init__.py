@@ -40,7 +40,10 @@ class Opts(ctypes.Structure):
                 ("timeout_ms", ctypes.c_double), ("block", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("fp64_gemm", ctypes.c_int32), ("fp64_symv", ctypes.c_int32),
                 ("qr_restart", ctypes.c_int32), ("inverse", ctypes.c_int32),
-                ("preserve_inputs", ctypes.c_int32), ("verify", ctypes.c_int32)]
+                ("preserve_inputs", ctypes.c_int32), ("verify", ctypes.c_int32), ("implicit", ctypes.c_int32),
+                ("wait_limit", ctypes.c_int32), ("start_block", ctypes.c_void_p), ("start_weights", ctypes.c_void_p),
+                ("start_cols", ctypes.c_int64), ("ld_start", ctypes.c_int64), ("filter_cut", ctypes.c_double),
+                ("filter_edge", ctypes.c_double), ("filter_degree", ctypes.c_int32), ("check_every", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -52,7 +55,11 @@ class Info(ctypes.Structure):
                [(f, ctypes.c_double) for f in ("gemm_ms", "gemm_flops", "gemm_bytes", "symv_ms", "symv_flops",
                                                 "symv_bytes", "orth_ms", "restart_ms", "ritz_ms")] + \
                [("inverse", ctypes.c_int64)] + \
-               [(f, ctypes.c_double) for f in ("max_eta", "orth_err")]
+               [(f, ctypes.c_double) for f in ("max_eta", "orth_err")] + \
+               [("gemm_core_launches", ctypes.c_int64)] + \
+               [(f, ctypes.c_double) for f in ("gemm_core_ms", "gemm_core_flops")] + \
+               [("diag_launches", ctypes.c_int64), ("diag_ms", ctypes.c_double), ("tnorm", ctypes.c_double),
+                ("filter_matvecs", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -170,9 +177,15 @@ class Solver:
         return st
 
     def set_options(self, **kw):
+        """Set fields of gsyeig_opts.  Device tensors for v0, start_block and
+        start_weights are kept alive by the solver; a column-major start_block
+        also sets start_cols and ld_start."""
         for k, v in kw.items():
-            if k == "v0":
-                self._v0 = v
+            if k in ("v0", "start_block", "start_weights"):
+                setattr(self, "_" + k, v)
+                if k == "start_block":
+                    self.opts.start_cols = 0 if v is None else v.shape[1]
+                    self.opts.ld_start = 0 if v is None else _ld(v, False)
                 v = None if v is None else v.data_ptr()
             setattr(self.opts, k, v)
         self._check(self.lib.gsyeig_set_options(self._h, ctypes.byref(self.opts)), "set_options")

@@ -62,7 +62,18 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // call has synchronised.  One profiler per handle, installed for the
 // duration of an API call on the calling thread.
 // ---------------------------------------------------------------------------
-enum ProfClass { PROF_GEMM = 0, PROF_SYMV = 1, PROF_ORTH = 2, PROF_RESTART = 3, PROF_RITZ = 4, PROF_NCLASS = 5 };
+// PROF_GEMM covers a whole GEMM-engine call (operand slicing included);
+// PROF_GEMM_CORE only the tensor-core kernel k_sliced_umma inside it.
+enum ProfClass {
+  PROF_GEMM = 0,
+  PROF_SYMV = 1,
+  PROF_ORTH = 2,
+  PROF_RESTART = 3,
+  PROF_RITZ = 4,
+  PROF_GEMM_CORE = 5,
+  PROF_DIAG = 6,  // the diagonal-block factor and inverse kernels of gs1
+  PROF_NCLASS = 7
+};
 
 struct KernelProfiler {
   std::vector<cudaEvent_t> pool;
@@ -99,6 +110,9 @@ int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64
           const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
           TriMode mode = TRI_ALL, int64_t diag = 0, const int *abort_flag = nullptr);
 
+// Elements of an M x N block inside the region `mode` writes.
+double region_elems(int64_t M, int64_t N, TriMode mode, int64_t diag);
+
 // How dgemm executes, installed per API call: sliced = true routes every
 // call to the error-free bf16 tensor-core GEMM, in slabs of K (tcgen05
 // engine gemm_umma.cu: up to 512, exact chunks of 128 inside; mma.sync
@@ -110,13 +124,15 @@ struct GemmContext {
   void *ws = nullptr;
   size_t ws_bytes = 0;
   int *err = nullptr;   // device flag: a bounded wait inside the tcgen05 engine expired
+  uint32_t spin = 0;    // poll limit of the engine's main-loop waits (0 = the default bound)
 };
 GemmContext *&current_gemm();
 
 size_t umma_workspace_bytes(int64_t M, int64_t N, int64_t K);
 int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
               const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
-              TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err);
+              TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err,
+              uint32_t spin);
 
 size_t sliced_workspace_bytes(int64_t M, int64_t N, int64_t K);
 int sliced_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
@@ -126,6 +142,9 @@ int sliced_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N,
 // Copy an M x N block (column-major, both with leading dimensions).
 int copy_block(cudaStream_t st, int64_t M, int64_t N, const double *src, int64_t lds, double *dst, int64_t ldd,
                const int *abort_flag = nullptr);
+
+// X = I (n x n, leading dimension ldx).
+int set_identity(cudaStream_t st, int64_t n, double *X, int64_t ldx);
 
 // Mirror one triangle of an n x n matrix into the other: lower_to_upper
 // copies A[i][j] (i > j) to A[j][i]; otherwise the reverse.
@@ -148,6 +167,9 @@ int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const doub
                   FactorWork &w, bool have_uinv);
 int trsm_back_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu, double *Y, int64_t ldy, int64_t s,
                       int nb, FactorWork &w, bool have_uinv);
+// X = U^-1 for the upper-triangular U (X n x n, ld ldx; zeros below the diagonal).
+int trtri_upper_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu, double *X, int64_t ldx, int nb,
+                        FactorWork &w, bool have_uinv);
 
 // ---------------------------------------------------------------------------
 // Operator application (symv.cu): z = C w, C full symmetric.

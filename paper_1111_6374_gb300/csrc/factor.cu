@@ -24,14 +24,21 @@ struct SmemBlock {
   __device__ double &operator()(int i, int j) { return p[i + j * ld]; }
 };
 
-// 1/d to within an ulp: FP32 seed, two Newton steps in FP64 (GB300's FP64
-// divide is a long dependent sequence on a narrow pipe).
+// 1/d to within an ulp for any positive finite d: d = f 2^k with f in
+// [1/2, 1) (frexp, exact), an FP32 seed of 1/f refined by two Newton steps
+// in FP64, then scaled back by 2^-k (ldexp, exact unless the result leaves
+// the FP64 range).  The reduction keeps the FP32 seed away from FP32's
+// overflow and subnormal ranges, which pivots of a pencil scaled by 2^+-140
+// reach.  GB300's FP64 divide is a long dependent sequence on a narrow pipe.
 __device__ __forceinline__ double recip(double d) {
-  double r = (double)(1.0f / (float)d);
-  double e = fma(-d, r, 1.0);
+  int k;
+  const double f = frexp(d, &k);
+  double r = (double)(1.0f / (float)f);
+  double e = fma(-f, r, 1.0);
   r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
+  e = fma(-f, r, 1.0);
+  r = fma(r, e, r);
+  return ldexp(r, -k);
 }
 
 // Factor the diagonal block B[k0:k0+kb, k0:k0+kb] (upper triangle) in
@@ -195,11 +202,14 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
       const int kb = (int)std::min<int64_t>(nb, J1 - k0);
       double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
       // U_kk (one CTA), then U_kk^-1 (one warp per column, many SMs)
+      KernelProfiler *prof = current_profiler();
+      const size_t e0 = prof ? prof->start(st) : SIZE_MAX;
       k_potrf_diag<<<1, DIAG_THREADS, sm, st>>>(B, ldb, k0, kb, nb, w.rdiag, w.flag);
       k_trtri_cols<<<dim3((unsigned)ceil_div(nb, INV_WARPS), 1), INV_WARPS * 32, sm, st>>>(n, B, ldb, k0, nb, w.rdiag,
                                                                                          Uinv_k, w.flag);
       count_launch(2);
       GS_CHECK_LAUNCH();
+      if (prof) prof->stop(st, e0, PROF_DIAG, 0.0, 0.0);
       const int64_t rest = n - k0 - kb;
       if (rest <= 0) break;
       double *Bk = &B[GS_IDX(k0, k0 + kb, ldb)];
@@ -267,6 +277,29 @@ int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const doub
                    ldu, 1.0, &A[GS_IDX(J1, J1, lda)], lda, TRI_LOWER, 0));
   }
   GS_TRY(symmetrize(st, n, A, lda, true));
+  return GSYEIG_SUCCESS;
+}
+
+// X = U^-1 (upper triangular, zeros below the diagonal) by the backward
+// block substitution U X = I restricted to the columns that can be nonzero:
+// block row k of X has nonzeros only in columns >= k0, so its update of the
+// rows above touches columns k0..n-1 only (n^3/3 flops in all).
+int trtri_upper_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu, double *X, int64_t ldx, int nb,
+                        FactorWork &w, bool have_uinv) {
+  if (!have_uinv) GS_TRY(trtri_diag_blocks(st, n, U, ldu, nb, w.Uinv));
+  GS_TRY(set_identity(st, n, X, ldx));
+  const int64_t last = ((n - 1) / nb) * nb;
+  for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
+    const int kb = (int)std::min<int64_t>(nb, n - k0);
+    const int64_t nc = n - k0;  // columns k0..n-1
+    const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
+    double *Xk = &X[GS_IDX(k0, k0, ldx)];
+    GS_TRY(dgemm(st, false, false, kb, nc, kb, 1.0, Uinv_k, nb, Xk, ldx, 0.0, w.panel, kb));
+    GS_TRY(copy_block(st, kb, nc, w.panel, kb, Xk, ldx));
+    if (k0 > 0)
+      GS_TRY(dgemm(st, false, false, k0, nc, kb, -1.0, &U[GS_IDX(0, k0, ldu)], ldu, w.panel, kb, 1.0,
+                   &X[GS_IDX(0, k0, ldx)], ldx));
+  }
   return GSYEIG_SUCCESS;
 }
 

@@ -194,6 +194,12 @@ __global__ void k_symmetrize(int64_t n, double *A, int64_t lda, bool lower_to_up
   }
 }
 
+__global__ void k_identity(int64_t n, double *__restrict__ X, int64_t ldx) {
+  for (int64_t j = blockIdx.y; j < n; j += gridDim.y)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      X[GS_IDX(i, j, ldx)] = (i == j) ? 1.0 : 0.0;
+}
+
 }  // namespace
 
 // sum_{j=0}^{N-1} clamp(a + j, 0, M)
@@ -235,7 +241,7 @@ int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64
         const double bk = (k0 == 0) ? beta : 1.0;
         if (gc->umma)
           GS_TRY(umma_gemm(st, transA, transB, M, N, kc, alpha, Ak, lda, Bk, ldb, bk, C, ldc, mode, diag, abort_flag,
-                           gc->ws, gc->ws_bytes, gc->err));
+                           gc->ws, gc->ws_bytes, gc->err, gc->spin));
         else
           GS_TRY(sliced_gemm(st, transA, transB, M, N, kc, alpha, Ak, lda, Bk, ldb, bk, C, ldc, mode, diag, abort_flag,
                              gc->ws, gc->ws_bytes));
@@ -264,6 +270,15 @@ int copy_block(cudaStream_t st, int64_t M, int64_t N, const double *src, int64_t
   if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(M, 256), 64), (unsigned)std::min<int64_t>(N, 4096));
   k_copy_block<<<grid, 256, 0, st>>>(M, N, src, lds, dst, ldd, abort_flag);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int set_identity(cudaStream_t st, int64_t n, double *X, int64_t ldx) {
+  if (n <= 0) return GSYEIG_SUCCESS;
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)std::min<int64_t>(n, 4096));
+  k_identity<<<grid, 256, 0, st>>>(n, X, ldx);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;

@@ -69,10 +69,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sptr(bar)), "r"(bytes) : "memory");
 }
 
-// bounded wait for the phase with the given parity; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait for the phase with the given parity (at most `limit` polls);
+// false on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = SPIN_LIMIT) {
   const uint32_t a = sptr(bar);
-  for (uint32_t it = 0; it < SPIN_LIMIT; it++) {
+  for (uint32_t it = 0; it < limit; it++) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -283,7 +284,7 @@ __device__ __forceinline__ bool failed(const int *f) { return *(volatile const i
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
     k_sliced_umma(TileGrid g, int64_t nks, const unsigned char *__restrict__ SA, const unsigned char *__restrict__ SB,
                   const int *__restrict__ ea, const int *__restrict__ eb, double alpha, double beta,
-                  double *__restrict__ C, int64_t ldc, const int *abort_flag, int *err) {
+                  double *__restrict__ C, int64_t ldc, const int *abort_flag, int *err, uint32_t spin) {
   if (abort_flag && *abort_flag) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *bufA = smem;                   // NBUF x A_STAGE
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         const unsigned char *gB = SB + (size_t)(n0 / UN) * nks * B_STAGE;
         for (int64_t ks = 0; ks < nks; ks++, it++) {
           const int b = (int)(it % NBUF);
-          if (it >= NBUF && !mbar_wait(&empty[b], (uint32_t)(((it / NBUF) - 1) & 1))) {
+          if (it >= NBUF && !mbar_wait(&empty[b], (uint32_t)(((it / NBUF) - 1) & 1), spin)) {
             atomicExch(&s_fail, 1);
             break;
           }
@@ -355,13 +356,13 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
           const bool first = (ks % CH_STAGES) == 0;  // first stage of an exact K chunk
           if (first) {
             // the epilogue has folded the previous chunk's accumulators out of TMEM
-            if (fc > 0 && !mbar_wait(acc_empty, (uint32_t)((fc - 1) & 1))) {
+            if (fc > 0 && !mbar_wait(acc_empty, (uint32_t)((fc - 1) & 1), spin)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           }
-          if (failed(&s_fail) || !mbar_wait(&full[b], (uint32_t)((it / NBUF) & 1))) {
+          if (failed(&s_fail) || !mbar_wait(&full[b], (uint32_t)((it / NBUF) & 1), spin)) {
             ok = false;
             break;
           }
@@ -419,12 +420,15 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         vl[c] = 0;
       }
       for (int64_t ch = 0; ch < nch; ch++, fc++) {
-        if (!mbar_wait(acc_full, (uint32_t)(fc & 1))) {
-          atomicExch(&s_fail, 1);
+        // the warp decides together (the TMEM loads and shuffles below are
+        // .sync.aligned: no lane may leave on its own)
+        const bool got = mbar_wait(acc_full, (uint32_t)(fc & 1), spin);
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0) atomicExch(&s_fail, 1);
           ok = false;
           break;
         }
-        if (failed(&s_fail)) {
+        if (__any_sync(0xffffffffu, failed(&s_fail))) {
           ok = false;
           break;
         }
@@ -528,7 +532,8 @@ size_t umma_workspace_bytes(int64_t M, int64_t N, int64_t K) {
 
 int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
               const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
-              TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err) {
+              TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err,
+              uint32_t spin) {
   if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
   if (K > UMMA_MAX_K || K <= 0) return GSYEIG_NOT_SUPPORTED;
   const int64_t Mpad = ceil_div(M, UM) * UM, Npad = ceil_div(N, UN) * UN, Kpad = ceil_div(K, KPAD) * KPAD;
@@ -551,10 +556,16 @@ int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, i
   // CTAs without an active tile (TRI modes) only set up and leave
   const int64_t tiles = (int64_t)g.mt * g.nt;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms());
+  KernelProfiler *prof = current_profiler();
+  const size_t e0 = prof ? prof->start(st) : SIZE_MAX;
   k_sliced_umma<<<grid, UMMA_THREADS, smem, st>>>(g, Kpad / UKS, P.SA, P.SB, P.ea, P.eb, alpha, beta, C, ldc,
-                                                  abort_flag, err);
+                                                  abort_flag, err, spin > 0 ? spin : SPIN_LIMIT);
   count_launch();
   GS_CHECK_LAUNCH();
+  if (prof) {
+    // the tensor-core kernel alone: 2K FP64-equivalent flops per written element
+    prof->stop(st, e0, PROF_GEMM_CORE, 2.0 * (double)K * region_elems(M, N, mode, diag), 0.0);
+  }
   return GSYEIG_SUCCESS;
 }
 

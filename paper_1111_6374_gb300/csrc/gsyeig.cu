@@ -57,8 +57,12 @@ struct gsyeig_ctx {
   DevBuf gemm_ws;         // slices of the tensor-core GEMM
   DevBuf gemm_err;        // device error flag of the tcgen05 engine
   DevBuf dfop, dfpart;    // double-float operator tiles and symv partials
-  DfOperator op;
+  DevBuf kinv, dfopL, kt; // variant KI: U^-1, the tiles of L = U^-T, two temporaries
+  DevBuf tmin;            // smallest eigenvalue of the final projected matrix
+  DevBuf wstart;          // start-block construction and Chebyshev filter vectors
+  DfOperator op, opL;
   bool use_df = false;
+  bool ki = false;        // the operator is U^-T G U^-1 applied implicitly (variant KI)
   KernelProfiler prof;
   GemmContext gemm;
 };
@@ -92,6 +96,11 @@ struct ProfScope {
     info->orth_ms = ms[PROF_ORTH];
     info->restart_ms = ms[PROF_RESTART];
     info->ritz_ms = ms[PROF_RITZ];
+    info->gemm_core_launches = l[PROF_GEMM_CORE];
+    info->gemm_core_ms = ms[PROF_GEMM_CORE];
+    info->gemm_core_flops = fl[PROF_GEMM_CORE];
+    info->diag_launches = l[PROF_DIAG];
+    info->diag_ms = ms[PROF_DIAG];
   }
   ~ProfScope() {
     if (on) {
@@ -146,6 +155,7 @@ int gemm_setup(gsyeig_handle h, int64_t n, int nb, int64_t s) {
     h->gemm.err = static_cast<int *>(h->gemm_err.p);
     GS_CUDA(cudaMemsetAsync(h->gemm.err, 0, sizeof(int), h->st));  // cudaMalloc does not zero
   }
+  h->gemm.spin = (uint32_t)h->opts.wait_limit;
   current_gemm() = &h->gemm;
   return GSYEIG_SUCCESS;
 }
@@ -213,13 +223,25 @@ struct ProfRegion {
   }
 };
 
+// The operator of ke1: z = C w with the explicit C (Eq. 3; double-float tiles
+// or FP64), or, for variant KI, z = U^-T (G (U^-1 w)) as L (G (L^T w)) with
+// L = U^-T held as lower-triangular double-float tiles.
+int apply_operator(gsyeig_handle h, cudaStream_t st, int64_t n, const double *C, int64_t ldc, const double *w,
+                   double *z) {
+  if (h->ki) {
+    double *t1 = h->kt.d(), *t2 = t1 + n;
+    GS_TRY(df_symv(st, h->opL, w, t1, DF_COLS));
+    GS_TRY(df_symv(st, h->op, t1, t2, DF_SYM));
+    return df_symv(st, h->opL, t2, z, DF_ROWS);
+  }
+  if (h->use_df) return df_symv(st, h->op, w, z);
+  return symv_f64(st, n, C, ldc, w, z);
+}
+
 // One Lanczos step j: z = C v_j, CGS2 against v_0..v_j, alpha_j, beta_j, v_{j+1}.
 int lanczos_step(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t m, int64_t j, const double *C, int64_t ldc) {
   double *V = h->V.d(), *z = h->z.d();
-  if (h->use_df)
-    GS_TRY(df_symv(st, h->op, V + (size_t)j * n, z));
-  else
-    GS_TRY(symv_f64(st, n, C, ldc, V + (size_t)j * n, z));
+  GS_TRY(apply_operator(h, st, n, C, ldc, V + (size_t)j * n, z));
   ProfRegion pr(st, PROF_ORTH);
   GS_TRY(lz_cgs2(st, n, j + 1, V, n, z, h->h1.d(), h->h2.d(), h->sq.d()));
   GS_TRY(lz_finalize(st, j, m, h->h1.d(), h->h2.d(), h->sq.d(), lz_nparts(n), h->alpha.d(), h->beta.d(),
@@ -239,11 +261,31 @@ int fresh_vector(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t ncols, uin
   return GSYEIG_SUCCESS;
 }
 
-// Implicitly restarted Lanczos on the full symmetric C (ke1, ke2, ke3).
+// Copies the device fault flags of the kernels in use (bounded waits of the
+// ke1 kernel and of the tensor-core GEMM) into f[0..1]; read them after the
+// next stream synchronisation.
+int fault_flags_async(gsyeig_handle h, cudaStream_t st, int f[2]) {
+  f[0] = f[1] = 0;
+  if (h->use_df || h->ki) GS_CUDA(cudaMemcpyAsync(&f[0], h->op.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GemmContext *gc = current_gemm();
+  if (gc && gc->sliced && gc->umma && gc->err)
+    GS_CUDA(cudaMemcpyAsync(&f[1], gc->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return GSYEIG_SUCCESS;
+}
+
+// Implicitly restarted Lanczos on the full symmetric C (ke1, ke2, ke3), or,
+// with Uinv != NULL, on U^-T C U^-1 applied implicitly (variant KI: C is
+// then the untransformed matrix G, Uinv the n x n inverse of the factor).
 // Output: the s wanted Ritz values (ascending) in theta_out (device) and
-// Ritz vectors in Y (n x s, ld ldy, device).
+// Ritz vectors in Y (n x s, ld ldy, device).  theta_min (host, optional):
+// the smallest eigenvalue of the final projected matrix, an upper bound on
+// the smallest eigenvalue of the operator.
+// A caller's start block X0 (opts.start_block, eigenvector approximations
+// of the pencil) is mapped to the operator's space by the upper-triangular
+// factor F (F = U of gs1; NULL: X0 is already in the operator's space).
 int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_t s, int which, double *theta_out,
-                double *Y, int64_t ldy, gsyeig_info *info, double *ms_ke3) {
+                double *Y, int64_t ldy, gsyeig_info *info, double *ms_ke3, const double *Uinv = nullptr,
+                double *theta_min = nullptr, const double *F = nullptr, int64_t ldf = 0) {
   cudaStream_t st = h->st;
   const LanczosParams P = lanczos_params(h->opts, n, s);
   const int64_t m = P.m, k = P.k, p = m - k;
@@ -267,8 +309,10 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
   GS_TRY(h->invw.ensure((size_t)5 * m * k * sizeof(double)));
   GS_TRY(h->state.ensure(sizeof(LanczosState)));
   double *V = h->V.d();
-  // ke1 operator: C's lower triangle as fp32 hi/lo tiles (default) or C itself
-  h->use_df = (h->opts.fp64_symv == 0);
+  // ke1 operator: C's lower triangle as fp32 hi/lo tiles (default) or C
+  // itself; variant KI: tiles of G and of L = U^-T
+  h->ki = (Uinv != nullptr);
+  h->use_df = (h->opts.fp64_symv == 0) || h->ki;
   if (h->use_df) {
     GS_TRY(h->dfop.ensure(df_operator_bytes(n)));
     GS_TRY(h->dfpart.ensure(df_partials_bytes(n)));
@@ -277,8 +321,16 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
     const int64_t NTt = ceil_div(n, 64);
     h->op.wsplit = h->op.W + (size_t)NTt * NTt * 64;
     h->op.err = reinterpret_cast<int *>(h->op.wsplit + (size_t)NTt * 64);
+    h->op.spin = (uint32_t)h->opts.wait_limit;
     GS_CUDA(cudaMemsetAsync(h->op.err, 0, sizeof(int), st));
     GS_TRY(df_operator_build(st, n, C, ldc, h->op));
+    if (h->ki) {
+      GS_TRY(h->dfopL.ensure(df_operator_bytes(n)));
+      GS_TRY(h->kt.ensure((size_t)2 * n * sizeof(double)));
+      h->opL = h->op;  // shares the partials, split vector and fault flag
+      h->opL.hi = static_cast<float *>(h->dfopL.p);
+      GS_TRY(df_operator_build(st, n, Uinv, n, h->opL, true, true));
+    }
   }
   LanczosState *dstate = static_cast<LanczosState *>(h->state.p);
   LanczosState hs;
@@ -287,9 +339,41 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
   GS_CUDA(cudaMemcpyAsync(dstate, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
   GS_CUDA(cudaMemsetAsync(h->beta.p, 0, (size_t)m * sizeof(double), st));
 
-  // v_0: the caller's start vector or a counter-based random one, normalised
-  if (h->opts.v0) GS_CUDA(cudaMemcpyAsync(h->z.p, h->opts.v0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  else GS_TRY(lz_random(st, n, h->opts.seed, 0, h->z.d()));
+  // v_0: built from the caller's start block, or the caller's start vector,
+  // or a counter-based random one; optionally Chebyshev-filtered; normalised
+  int64_t filter_mv = 0;
+  const gsyeig_opts &o = h->opts;
+  if (o.start_block && o.start_cols > 0) {
+    if (o.ld_start < n) return GSYEIG_NOT_SUPPORTED;
+    GS_TRY(h->wstart.ensure((size_t)3 * n * sizeof(double)));
+    double *t = h->wstart.d();
+    GS_TRY(lz_weighted_sum(st, n, o.start_cols, o.start_block, o.ld_start, o.start_weights, F ? t : h->z.d()));
+    if (F) GS_TRY(lz_trmv_upper(st, n, F, ldf, t, h->z.d()));
+  } else if (o.v0) {
+    GS_CUDA(cudaMemcpyAsync(h->z.p, o.v0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    GS_TRY(lz_random(st, n, o.seed, 0, h->z.d()));
+  }
+  if (o.filter_degree > 0) {
+    // Chebyshev filter p_d(C) z damping the unwanted end [cut, edge]
+    // (Zhou and Saad's filtered subspace iteration, 2007): components below
+    // the cut (above it, for the largest pairs) grow like T_d, the rest stay
+    // bounded by 1
+    GS_TRY(h->wstart.ensure((size_t)3 * n * sizeof(double)));
+    double *y0 = h->wstart.d(), *y1 = y0 + n, *cy = y0 + 2 * n;
+    const double a = std::min(o.filter_cut, o.filter_edge), b = std::max(o.filter_cut, o.filter_edge);
+    const double e = 0.5 * (b - a), c = 0.5 * (b + a);
+    GS_CUDA(cudaMemcpyAsync(y0, h->z.p, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    double *yp = y0, *yc = y1;
+    for (int i = 1; i <= o.filter_degree; i++) {
+      GS_TRY(apply_operator(h, st, n, C, ldc, i == 1 ? yp : yc, cy));
+      // y_1 = (C - c) y_0 / e;  y_{i+1} = 2 (C - c) y_i / e - y_{i-1}
+      GS_TRY(lz_cheb_step(st, n, cy, i == 1 ? yp : yc, yp, c, e, i == 1, i == 1 ? yc : yp));
+      if (i > 1) std::swap(yp, yc);
+      filter_mv++;
+    }
+    GS_CUDA(cudaMemcpyAsync(h->z.p, yc, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
   GS_TRY(lz_cgs2(st, n, 0, V, n, h->z.d(), h->h1.d(), h->h2.d(), h->sq.d()));
   GS_TRY(lz_norm_finish(st, h->sq.d(), (int)np, dstate, nullptr));
   GS_TRY(lz_scale_into(st, n, h->z.d(), V, dstate));
@@ -304,11 +388,73 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
   int64_t j0 = 0, restarts = 0, matvecs = 0, breakdowns = 0;
   int status = GSYEIG_SUCCESS;
   auto t_start = std::chrono::steady_clock::now();
-  for (;;) {
-    for (int64_t j = j0; j < m; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
-    matvecs += m - j0;
+  int fault[2];
+  // Ritz pairs of the leading mc x mc projected matrix (mc = m at the end of
+  // a cycle; smaller at an early check) and the convergence test
+  auto ritz = [&](int64_t mc) -> int {
+    ProfRegion pr(st, PROF_RITZ);
+    if (thick) {
+      // the k kept Ritz pairs (the s wanted among them); M has an arrow after a restart
+      const int64_t kf = (which == GSYEIG_LARGEST) ? mc - k : 0;
+      GS_TRY(tri_bisect(st, mc, h->alpha.d(), h->beta.d(), ka, h->arrow.d(), kf, k, h->theta.d()));
+      GS_TRY(tri_invit(st, mc, h->alpha.d(), h->beta.d(), ka, h->arrow.d(), k, h->theta.d(), h->S.d(), m,
+                       h->invw.d()));
+    } else {
+      const int64_t wfc = (which == GSYEIG_LARGEST) ? mc - s : 0;
+      GS_TRY(tri_bisect(st, mc, h->alpha.d(), h->beta.d(), 0, nullptr, 0, mc, h->theta.d()));
+      GS_TRY(tri_invit(st, mc, h->alpha.d(), h->beta.d(), 0, nullptr, s, h->theta.d() + wfc, h->S.d(), m,
+                       h->invw.d()));
+    }
+    GS_TRY(tri_converged(st, mc, s, h->theta.d(), h->beta.d(), h->S.d() + (size_t)woff * m, m, h->opts.tol, dstate));
     GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    GS_TRY(fault_flags_async(h, st, fault));
     GS_CUDA(cudaStreamSynchronize(st));
+    if (fault[0] || fault[1]) return GSYEIG_TIMEOUT;
+    return GSYEIG_SUCCESS;
+  };
+  const int64_t ce = h->opts.check_every;        // 0: test only at the end of a cycle
+  const int64_t first_check = thick ? k + 1 : s;  // smallest projected matrix holding the kept pairs
+  int64_t mc = m;                                 // order of the projected matrix of the final Ritz pairs
+  bool early = false;
+  for (;;) {
+    int64_t j = j0;
+    bool stop_pass = false;
+    while (j < m) {
+      int64_t jend = m;
+      if (ce > 0) {
+        jend = std::max(j0 + ((j - j0) / ce + 1) * ce, first_check);
+        jend = std::min(std::max(jend, j + 1), m);
+      }
+      const int64_t jb = j;
+      for (; j < jend; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
+      matvecs += jend - jb;
+      if (jend == m) break;
+      // an early convergence test on the leading jend x jend matrix
+      GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
+      GS_TRY(fault_flags_async(h, st, fault));
+      GS_CUDA(cudaStreamSynchronize(st));
+      if (fault[0] || fault[1]) return GSYEIG_TIMEOUT;
+      if (hs.breakdown_at >= 0) {
+        stop_pass = true;  // handled below, as at the end of a cycle
+        break;
+      }
+      GS_TRY(ritz(jend));
+      if (hs.nconv >= s) {
+        mc = jend;
+        early = true;
+        break;
+      }
+    }
+    if (early) break;
+    if (stop_pass) {
+      // finish the cycle's bookkeeping the same way as a full pass: the steps
+      // after a breakdown were no-ops
+      for (; j < m; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
+    }
+    GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    GS_TRY(fault_flags_async(h, st, fault));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (fault[0] || fault[1]) return GSYEIG_TIMEOUT;  // a bounded device wait ran out: results invalid
     if (hs.breakdown_at >= 0 && hs.breakdown_at < m - 1) {
       // invariant subspace met: continue from a fresh random direction
       const int64_t b = hs.breakdown_at;
@@ -321,22 +467,7 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
       continue;
     }
     // Ritz values of T_m, vectors of the wanted ones, convergence test
-    {
-      ProfRegion pr(st, PROF_RITZ);
-      if (thick) {
-        // the k kept Ritz pairs (the s wanted among them); M has an arrow after a restart
-        GS_TRY(tri_bisect(st, m, h->alpha.d(), h->beta.d(), ka, h->arrow.d(), kfirst, k, h->theta.d()));
-        GS_TRY(tri_invit(st, m, h->alpha.d(), h->beta.d(), ka, h->arrow.d(), k, h->theta.d(), h->S.d(), m,
-                         h->invw.d()));
-      } else {
-        GS_TRY(tri_bisect(st, m, h->alpha.d(), h->beta.d(), 0, nullptr, 0, m, h->theta.d()));
-        GS_TRY(tri_invit(st, m, h->alpha.d(), h->beta.d(), 0, nullptr, s, h->theta.d() + wf, h->S.d(), m,
-                         h->invw.d()));
-      }
-      GS_TRY(tri_converged(st, m, s, h->theta.d(), h->beta.d(), h->S.d() + (size_t)woff * m, m, h->opts.tol, dstate));
-    }
-    GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
-    GS_CUDA(cudaStreamSynchronize(st));
+    GS_TRY(ritz(m));
     if (hs.nconv >= s) break;
     if (restarts >= h->opts.max_restarts) {
       status = GSYEIG_NO_CONVERGENCE;
@@ -379,21 +510,26 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
     restarts++;
     j0 = k;
   }
-  // ke3: Ritz vectors Y = V_m S
+  if (theta_min) {
+    // the projected matrix of the last cycle is still in (alpha, beta, arrow)
+    GS_TRY(h->tmin.ensure(sizeof(double)));
+    const int64_t kam = thick ? ka : 0;
+    GS_TRY(tri_bisect(st, mc, h->alpha.d(), h->beta.d(), kam, kam > 0 ? h->arrow.d() : nullptr, 0, 1, h->tmin.d()));
+    GS_CUDA(cudaMemcpyAsync(theta_min, h->tmin.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  // ke3: Ritz vectors Y = V_mc S
   cudaEvent_t e0 = h->ev[5], e1 = h->ev[6];
   GS_CUDA(cudaEventRecord(e0, st));
-  GS_TRY(dgemm(st, false, false, n, s, m, 1.0, V, n, h->S.d() + (size_t)woff * m, m, 0.0, Y, ldy));
-  GS_CUDA(cudaMemcpyAsync(theta_out, h->theta.d() + (thick ? woff : wf), (size_t)s * sizeof(double),
-                          cudaMemcpyDeviceToDevice, st));
+  GS_TRY(dgemm(st, false, false, n, s, mc, 1.0, V, n, h->S.d() + (size_t)woff * m, m, 0.0, Y, ldy));
+  const int64_t wfin = thick ? woff : ((which == GSYEIG_LARGEST) ? mc - s : 0);
+  GS_CUDA(cudaMemcpyAsync(theta_out, h->theta.d() + wfin, (size_t)s * sizeof(double), cudaMemcpyDeviceToDevice, st));
   GS_CUDA(cudaEventRecord(e1, st));
   GS_CUDA(cudaEventSynchronize(e1));
   if (ms_ke3) *ms_ke3 = elapsed(e0, e1);
-  if (h->use_df) {
-    // a bounded wait inside the symv kernel that ran out invalidates the result
-    int e = 0;
-    GS_CUDA(cudaMemcpy(&e, h->op.err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) return GSYEIG_TIMEOUT;
-  }
+  // a bounded wait that ran out inside the symv kernel or the GEMM engine invalidates the result
+  GS_TRY(fault_flags_async(h, st, fault));
+  GS_CUDA(cudaStreamSynchronize(st));
+  if (fault[0] || fault[1]) return GSYEIG_TIMEOUT;
   if (info) {
     info->nconv = hs.nconv;
     info->restarts = restarts;
@@ -402,6 +538,9 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
     info->keep = k;
     info->breakdowns = breakdowns;
     info->max_ritz_estimate = hs.max_est;
+    info->tnorm = hs.tnorm;
+    info->filter_matvecs = filter_mv;
+    info->matvecs = matvecs + filter_mv;
   }
   return status;
 }
@@ -466,7 +605,7 @@ int gsyeig_destroy(gsyeig_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
-  DevBuf *bufs[] = {&h->pA, &h->pB, &h->vA, &h->vB, &h->vws, &h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
+  DevBuf *bufs[] = {&h->wstart, &h->kinv, &h->dfopL, &h->kt, &h->tmin, &h->pA, &h->pB, &h->vA, &h->vB, &h->vws, &h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
                     &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
                     &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
   for (DevBuf *b : bufs) b->release();
@@ -485,7 +624,10 @@ int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
       o->block < 0 || o->block > 160 || (o->block > 0 && o->block < 16) || o->profile < 0 || o->profile > 1 ||
       o->fp64_gemm < 0 || o->fp64_gemm > 2 || o->fp64_symv < 0 || o->fp64_symv > 1 || o->qr_restart < 0 ||
       o->qr_restart > 1 || o->inverse < 0 || o->inverse > 1 || o->preserve_inputs < 0 ||
-      o->preserve_inputs > 1 || o->verify < 0 || o->verify > 1)
+      o->preserve_inputs > 1 || o->verify < 0 || o->verify > 1 || o->implicit < 0 || o->implicit > 1 ||
+      o->wait_limit < 0 || o->filter_degree < 0 || o->filter_degree > 64 || o->check_every < 0 ||
+      o->start_cols < 0 || (o->start_block && o->start_cols > 0 && o->ld_start < 1) ||
+      (o->filter_degree > 0 && !(o->filter_cut != o->filter_edge)))
     return -2;
   if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
   h->opts = *o;
@@ -553,8 +695,28 @@ int gsyeig_symv(gsyeig_handle h, const double *dC, int64_t ldc, int64_t n, const
   if (!dw) return -5;
   if (!dz) return -6;
   GS_TRY(begin(h));
-  GS_TRY(symv_f64(h->st, n, dC, ldc, dw, dz));
-  return finish(h);
+  ProfScope prof(h);
+  if (h->opts.fp64_symv == 1) {
+    GS_TRY(symv_f64(h->st, n, dC, ldc, dw, dz));
+    return finish(h);
+  }
+  // the solver's default ke1 operator: C's lower triangle as fp32 hi/lo tiles
+  GS_TRY(h->dfop.ensure(df_operator_bytes(n)));
+  GS_TRY(h->dfpart.ensure(df_partials_bytes(n)));
+  DfOperator op;
+  op.hi = static_cast<float *>(h->dfop.p);
+  op.W = static_cast<float2 *>(h->dfpart.p);
+  const int64_t NTt = ceil_div(n, 64);
+  op.wsplit = op.W + (size_t)NTt * NTt * 64;
+  op.err = reinterpret_cast<int *>(op.wsplit + (size_t)NTt * 64);
+  op.spin = (uint32_t)h->opts.wait_limit;
+  GS_CUDA(cudaMemsetAsync(op.err, 0, sizeof(int), h->st));
+  GS_TRY(df_operator_build(h->st, n, dC, ldc, op));
+  GS_TRY(df_symv(h->st, op, dw, dz));
+  int e = 0;
+  GS_CUDA(cudaMemcpyAsync(&e, op.err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  GS_TRY(finish(h));
+  return e ? GSYEIG_TIMEOUT : GSYEIG_SUCCESS;
 }
 
 int gsyeig_trsm_back(gsyeig_handle h, const double *dU, int64_t ldu, int64_t n, double *dY, int64_t ldy, int64_t s) {
@@ -713,6 +875,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     GS_TRY(potrf_blocked(st, n, dA, dlda, nb, fw));
     GS_CUDA(cudaMemcpyAsync(&flag, fw.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
+    GS_TRY(gemm_check(h));  // an expired GEMM wait, not a pivot, may have set the flag
     if (flag) {  // A indefinite: put its diagonal back, take the direct route
       GS_CUDA(cudaMemcpy2DAsync(dA, (size_t)(dlda + 1) * sizeof(double), h->diag.p, sizeof(double), sizeof(double), n,
                                 cudaMemcpyDeviceToDevice, st));
@@ -734,17 +897,37 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   }
   GS_CUDA(cudaEventRecord(h->ev[2], st));
   GS_CUDA(cudaStreamSynchronize(st));
+  GS_TRY(gemm_check(h));
   if (flag) {
     if (info) info->potrf_index = flag;
     return GSYEIG_NOT_SPD;
   }
-  // gs2: C = U^-T G U^-1 over G (diagonal-block inverses reused from gs1)
-  GS_TRY(sygst_blocked(st, n, dG, dldg, dF, dldf, nb, fw, true));
+  const bool ki = h->opts.implicit == 1;
+  if (ki && h->opts.fp64_symv == 1) return GSYEIG_NOT_SUPPORTED;  // KI runs on the double-float tiles
+  if (!ki) {
+    // gs2: C = U^-T G U^-1 over G (diagonal-block inverses reused from gs1)
+    GS_TRY(sygst_blocked(st, n, dG, dldg, dF, dldf, nb, fw, true));
+  } else {
+    // variant KI: G stays; U^-1 is formed once (n^3/3 flops on the GEMM
+    // engine) so that both triangular solves of every step become
+    // triangular products over stored tiles
+    if (!inv) GS_TRY(symmetrize(st, n, dG, dldg, true));  // A's lower triangle is the one read
+    GS_TRY(h->kinv.ensure((size_t)n * n * sizeof(double)));
+    GS_TRY(trtri_upper_blocked(st, n, dF, dldf, h->kinv.d(), n, nb, fw, true));
+  }
   GS_CUDA(cudaEventRecord(h->ev[3], st));
-  // ke: Lanczos on C; Ritz vectors land in X
-  double ms_ke3 = 0;
-  int status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3);
+  // ke: Lanczos on C; Ritz vectors land in X.  On the inverse route the
+  // smallest Ritz value of the final projected matrix bounds the smallest
+  // eigenvalue of L^-T B L^-1 from above: if it is not positive, B is not
+  // positive definite (the direct route's Cholesky of B would fail).
+  double ms_ke3 = 0, theta_min = 1.0;
+  int status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
+                           ki ? h->kinv.d() : nullptr, inv ? &theta_min : nullptr);
   if (status != GSYEIG_SUCCESS && status != GSYEIG_NO_CONVERGENCE && status != GSYEIG_TIMEOUT) return status;
+  if (inv && !(theta_min > 0.0)) {
+    if (info) info->inverse = 1;
+    return GSYEIG_NOT_SPD;
+  }
   GS_CUDA(cudaEventRecord(h->ev[4], st));
   // bt1: X = U^-1 Y
   GS_TRY(trsm_back_blocked(st, n, dF, dldf, dX, dldx, s, nb, fw, true));

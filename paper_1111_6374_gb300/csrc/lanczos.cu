@@ -194,7 +194,58 @@ __global__ void k_invert_vals(int64_t s, double *theta) {
   }
 }
 
+__global__ void k_weighted_sum(int64_t n, int64_t k, const double *__restrict__ X, int64_t ldx,
+                               const double *__restrict__ w, double *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t c = 0; c < k; c++) acc = fma(X[(size_t)c * ldx + i], w ? w[c] : 1.0, acc);
+    out[i] = acc;
+  }
+}
+
+// row i of U v over columns j >= i; lanes of a warp take consecutive rows,
+// so every column's reads are coalesced
+__global__ void k_trmv_upper(int64_t n, const double *__restrict__ U, int64_t ldu, const double *__restrict__ v,
+                             double *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t j = i; j < n; j++) acc = fma(U[i + (size_t)j * ldu], v[j], acc);
+    out[i] = acc;
+  }
+}
+
+__global__ void k_cheb_step(int64_t n, const double *__restrict__ Cy, const double *__restrict__ y,
+                            const double *yprev, double c, double inv_e, int first, double *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = (Cy[i] - c * y[i]) * inv_e;
+    out[i] = first ? t : 2.0 * t - yprev[i];
+  }
+}
+
 }  // namespace
+
+int lz_weighted_sum(cudaStream_t st, int64_t n, int64_t k, const double *X, int64_t ldx, const double *w,
+                    double *out) {
+  k_weighted_sum<<<grid1d(n, 256), 256, 0, st>>>(n, k, X, ldx, w, out);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int lz_trmv_upper(cudaStream_t st, int64_t n, const double *U, int64_t ldu, const double *v, double *out) {
+  k_trmv_upper<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(n, U, ldu, v, out);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int lz_cheb_step(cudaStream_t st, int64_t n, const double *Cy, const double *y, const double *yprev, double c,
+                 double e, bool first, double *out) {
+  k_cheb_step<<<grid1d(n, 256), 256, 0, st>>>(n, Cy, y, yprev, c, 1.0 / e, first ? 1 : 0, out);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
 
 int lz_nparts(int64_t n) { return (int)ceil_div(n, SUB_ROWS); }
 

@@ -38,6 +38,16 @@ int lz_thick_restart(cudaStream_t st, int64_t m, int64_t k, const double *theta,
 // (A, B): X column i <- X column s-1-i / sqrt(theta[s-1-i]) and
 // theta[i] <- 1 / theta[s-1-i], so lambda ascends and X^T B X = I.
 int lz_invert_pairs(cudaStream_t st, int64_t n, int64_t s, double *theta, double *X, int64_t ldx);
+// out = X w (X n x k, ld ldx; w device, k entries, NULL = all ones).
+int lz_weighted_sum(cudaStream_t st, int64_t n, int64_t k, const double *X, int64_t ldx, const double *w,
+                    double *out);
+// out = U v for the upper triangle of U (n x n, ld ldu); the strictly lower
+// triangle of U is not read.
+int lz_trmv_upper(cudaStream_t st, int64_t n, const double *U, int64_t ldu, const double *v, double *out);
+// One step of the Chebyshev recurrence on [c - e, c + e]: out = (Cy - c y) / e
+// when first, else out = 2 (Cy - c y) / e - yprev (out may alias yprev).
+int lz_cheb_step(cudaStream_t st, int64_t n, const double *Cy, const double *y, const double *yprev, double c,
+                 double e, bool first, double *out);
 int lz_restart_residual(cudaStream_t st, int64_t n, int64_t k, int64_t m, const double *Vq, int64_t ldvq,
                         const double *vm, const double *betaP, const double *beta, const double *Q, int64_t ldq,
                         double *f);

@@ -50,8 +50,12 @@ __device__ __forceinline__ void acc2(float &s, float &c, float p, float e) {
   c += q + e;
 }
 
-__global__ void k_op_build(int64_t n, int64_t NT, const double *__restrict__ C, int64_t ldc, float *__restrict__ hi,
-                           float *__restrict__ lo) {
+// Tiles of the lower triangle of M: M = C (trans = 0) or M = C^T (trans =
+// 1, read from C's upper triangle); with tri = 1 the entries above the
+// diagonal of the diagonal tiles are stored as zeros (M lower triangular),
+// else the diagonal tiles hold the full symmetric block.
+__global__ void k_op_build(int64_t n, int64_t NT, const double *__restrict__ C, int64_t ldc, int tri, int trans,
+                           float *__restrict__ hi, float *__restrict__ lo) {
   const int64_t bi = blockIdx.y, bj = blockIdx.x;
   if (bj > bi) return;
   const int64_t t = bi * (bi + 1) / 2 + bj;
@@ -60,7 +64,7 @@ __global__ void k_op_build(int64_t n, int64_t NT, const double *__restrict__ C, 
     const int r = idx % TS, c = idx / TS;
     const int64_t i = bi * TS + r, j = bj * TS + c;
     double v = 0.0;
-    if (i < n && j < n) v = C[i + j * ldc];
+    if (i < n && j < n && !(tri && j > i)) v = trans ? C[j + i * ldc] : C[i + j * ldc];
     const float vh = (float)v;
     const int pos = (r ^ (c & 31)) + TS * c;
     h[pos] = vh;
@@ -94,9 +98,11 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
 
 __device__ __forceinline__ uint32_t sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// bounded mbarrier wait (false on expiry)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 24); it++) {
+constexpr uint32_t SPIN_LIMIT = 1u << 24;
+
+// bounded mbarrier wait, at most `limit` polls (false on expiry)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; it++) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -122,10 +128,14 @@ constexpr int TILE_BYTES = TS * TS * 4;  // one of hi / lo
 // Persistent CTAs; tiles t = blockIdx.x + i gridDim.x.  Thread 0 keeps
 // NSTAGE tiles in flight with cp.async.bulk (hi and lo, 16 KB each) into
 // shared memory; all 8 warps compute on the oldest one.  A wait that runs
-// out sets *err and ends the CTA after draining its own copies.
+// out (after `spin` polls) sets *err and ends the CTA after draining its own
+// copies (those waits keep the full bound).
+// mode DF_SYM: z = M w for the symmetric M whose lower triangle is stored
+// (row sums of every tile, column sums of the off-diagonal ones);
+// DF_ROWS: z = L w and DF_COLS: z = L^T w for the lower-triangular L stored.
 __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, const float *__restrict__ hi,
                                                         const float *__restrict__ lo, const float2 *__restrict__ ws,
-                                                        float2 *__restrict__ W, int *err) {
+                                                        float2 *__restrict__ W, int *err, int mode, uint32_t spin) {
   extern __shared__ __align__(128) unsigned char smem[];
   float *sh = reinterpret_cast<float *>(smem);                       // NSTAGE x (hi tile, lo tile)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)NSTAGE * 2 * TILE_BYTES);
@@ -164,34 +174,38 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
     int bi, bj;
     tile_of(t, bi, bj);
     const bool diag = (bi == bj);
+    const bool do_rows = mode != DF_COLS;                          // block-uniform
+    const bool do_cols = (mode == DF_SYM && !diag) || mode == DF_COLS;
     if (threadIdx.x < TS) xr[threadIdx.x] = ws[(int64_t)bj * TS + threadIdx.x];
     else if (threadIdx.x < 2 * TS) xc[threadIdx.x - TS] = ws[(int64_t)bi * TS + threadIdx.x - TS];
     const int b = i % NSTAGE;
-    const bool ok = mbar_wait(&full[b], (uint32_t)((i / NSTAGE) & 1));
+    const bool ok = mbar_wait(&full[b], (uint32_t)((i / NSTAGE) & 1), spin);
     if (!ok) s_fail = 1;
     __syncthreads();
     if (s_fail) break;
     const float *h = sh + (size_t)(b * 2) * TS * TS, *l = h + TS * TS;
     float ch[16], cl[16];
-    // row sums: thread (row r, column group g) over columns 16 g .. 16 g + 15
+    if (do_rows) {
+      // row sums: thread (row r, column group g) over columns 16 g .. 16 g + 15
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-      const int col = g * 16 + k, pos = (r ^ (col & 31)) + TS * col;
-      ch[k] = h[pos];
-      cl[k] = l[pos];
-    }
-    float rs = 0.f, rc = 0.f;
+      for (int k = 0; k < 16; k++) {
+        const int col = g * 16 + k, pos = (r ^ (col & 31)) + TS * col;
+        ch[k] = h[pos];
+        cl[k] = l[pos];
+      }
+      float rs = 0.f, rc = 0.f;
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-      const float2 x = xr[g * 16 + k];
-      float p, e;
-      two_prod(ch[k], x.x, p, e);
-      e = fmaf(ch[k], x.y, e);
-      e = fmaf(cl[k], x.x, e);
-      acc2(rs, rc, p, e);
+      for (int k = 0; k < 16; k++) {
+        const float2 x = xr[g * 16 + k];
+        float p, e;
+        two_prod(ch[k], x.x, p, e);
+        e = fmaf(ch[k], x.y, e);
+        e = fmaf(cl[k], x.x, e);
+        acc2(rs, rc, p, e);
+      }
+      rowp[g][r] = make_float2(rs, rc);
     }
-    rowp[g][r] = make_float2(rs, rc);
-    if (!diag) {
+    if (do_cols) {
       // column sums (C_ij^T w_i): thread (column c = r, row group g) over
       // rows 16 g .. 16 g + 15, read across the swizzle without conflicts
       const int c = r;
@@ -218,12 +232,12 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
       issue(issued);
       issued++;
     }
-    if (threadIdx.x < TS) {
+    if (do_rows && threadIdx.x < TS) {
       // rows of block bi: combine the 4 column groups
       const int rr = threadIdx.x;
       float2 a = df_add(df_add(rowp[0][rr], rowp[1][rr]), df_add(rowp[2][rr], rowp[3][rr]));
       W[(int64_t)bj * npad + (int64_t)bi * TS + rr] = a;
-    } else if (!diag && threadIdx.x < 2 * TS) {
+    } else if (do_cols && threadIdx.x >= TS && threadIdx.x < 2 * TS) {
       const int cc = threadIdx.x - TS;
       W[(int64_t)bi * npad + (int64_t)bj * TS + cc] = df_add(df_add(colp[0][cc], colp[1][cc]), df_add(colp[2][cc], colp[3][cc]));
     }
@@ -232,22 +246,26 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
   if (threadIdx.x == 0) {
     // none of our bulk copies may still be landing when the CTA exits
     for (int i = (issued > NSTAGE ? issued - NSTAGE : 0); i < issued; i++)
-      if (!mbar_wait(&full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1))) s_fail = 1;
+      if (!mbar_wait(&full[i % NSTAGE], (uint32_t)((i / NSTAGE) & 1), SPIN_LIMIT)) s_fail = 1;
     if (s_fail) atomicExch(err, 1);
   }
 }
 
-// z_i = sum over the NT slots of W[slot][i], accumulated in double-float and
-// rounded to FP64 once.
-__global__ void k_reduce_slots(int64_t n, int64_t npad, int64_t NT, const float2 *__restrict__ W, double *__restrict__ z) {
+// z_i = sum over the slots of W[slot][i] written for row i (all NT for
+// DF_SYM; the tiles' column blocks 0..b for DF_ROWS and b..NT-1 for DF_COLS,
+// b = i / 64), accumulated in double-float and rounded to FP64 once.
+__global__ void k_reduce_slots(int64_t n, int64_t npad, int64_t NT, const float2 *__restrict__ W, double *__restrict__ z,
+                               int mode) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-    int64_t q = 0;
-    for (; q + 1 < NT; q += 2) {
+    const int64_t blk = i / TS;
+    int64_t q = (mode == DF_COLS) ? blk : 0;
+    const int64_t q1 = (mode == DF_ROWS) ? blk + 1 : NT;
+    for (; q + 1 < q1; q += 2) {
       a = df_add(a, W[q * npad + i]);
       b = df_add(b, W[(q + 1) * npad + i]);
     }
-    if (q < NT) a = df_add(a, W[q * npad + i]);
+    if (q < q1) a = df_add(a, W[q * npad + i]);
     a = df_add(a, b);
     z[i] = (double)a.x + (double)a.y;
   }
@@ -265,20 +283,36 @@ size_t df_partials_bytes(int64_t n) {
   return (size_t)NT * NT * TS * sizeof(float2) + (size_t)NT * TS * sizeof(float2) + 256;
 }
 
-int df_operator_build(cudaStream_t st, int64_t n, const double *C, int64_t ldc, DfOperator &op) {
+int df_operator_build(cudaStream_t st, int64_t n, const double *C, int64_t ldc, DfOperator &op, bool tri, bool trans) {
   const int64_t NT = ceil_div(n, TS);
   op.n = n;
   op.NT = NT;
   op.npad = NT * TS;
   const size_t tiles = (size_t)NT * (NT + 1) / 2 * TS * TS;
   op.lo = op.hi + tiles;
-  k_op_build<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, NT, C, ldc, op.hi, op.lo);
+  k_op_build<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, NT, C, ldc, tri ? 1 : 0, trans ? 1 : 0, op.hi, op.lo);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
 }
 
-int df_symv(cudaStream_t st, const DfOperator &op, const double *w, double *z) {
+int num_sms_cached() {
+  static int sms[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (sms[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 1;
+    }
+    sms[dev] = v > 0 ? v : 1;
+  }
+  return sms[dev];
+}
+
+int df_symv(cudaStream_t st, const DfOperator &op, const double *w, double *z, int mode) {
   KernelProfiler *prof = current_profiler();
   size_t e0 = prof ? prof->start(st) : SIZE_MAX;
   const int64_t ntiles = op.NT * (op.NT + 1) / 2;
@@ -286,16 +320,17 @@ int df_symv(cudaStream_t st, const DfOperator &op, const double *w, double *z) {
       op.n, op.npad, w, op.wsplit);
   const size_t smem = (size_t)NSTAGE * 2 * TILE_BYTES + NSTAGE * sizeof(uint64_t);
   GS_CUDA(cudaFuncSetAttribute((const void *)k_symv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, 152 * CTAS_PER_SM), DF_THREADS, smem, st>>>((int)op.NT, op.npad, op.hi, op.lo,
-                                                                                    op.wsplit, op.W, op.err);
+  k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, (int64_t)num_sms_cached() * CTAS_PER_SM), DF_THREADS, smem, st>>>(
+      (int)op.NT, op.npad, op.hi, op.lo, op.wsplit, op.W, op.err, mode, op.spin > 0 ? op.spin : SPIN_LIMIT);
   k_reduce_slots<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.n, 256), 1024)), 256, 0, st>>>(
-      op.n, op.npad, op.NT, op.W, z);
+      op.n, op.npad, op.NT, op.W, z, mode);
   count_launch(3);
   GS_CHECK_LAUNCH();
   if (prof) {
     const double n = (double)op.n;
-    // algorithmic: 2n^2 flops; the stored triangle (hi + lo, 8 bytes per entry of n(n+1)/2) plus w and z
-    prof->stop(st, e0, PROF_SYMV, 2.0 * n * n, 8.0 * (n * (n + 1) / 2) + 16.0 * n);
+    // algorithmic: 2n^2 flops (n^2 for a triangular product); the stored
+    // triangle (hi + lo, 8 bytes per entry of n(n+1)/2) plus w and z
+    prof->stop(st, e0, PROF_SYMV, (mode == DF_SYM ? 2.0 : 1.0) * n * n, 8.0 * (n * (n + 1) / 2) + 16.0 * n);
   }
   return GSYEIG_SUCCESS;
 }

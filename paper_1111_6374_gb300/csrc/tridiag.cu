@@ -421,8 +421,10 @@ int tri_converged(cudaStream_t st, int64_t m, int64_t cnt, const double *theta_a
 //
 // Host code may not use g_noalloc_scratch directly: on the host that name
 // is a stand-in symbol, not a device address.  The device address is looked
-// up once per device with cudaGetSymbolAddress, with that device current,
-// on the first call made on that device.
+// up with cudaGetSymbolAddress, with that device current, by each call (a
+// lookup allocates nothing; a device reset followed by a new context may
+// move the array) and kept per device; the first call on a device does
+// this set-up.
 // ---------------------------------------------------------------------------
 namespace gs {
 namespace {
@@ -435,14 +437,16 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 std::mutex g_noalloc_mutex;
 double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set-up on
-// first use per device).
-int noalloc_scratch(double **out) {
+// Device address of the scratch array on the current device: looked up
+// afresh unless `st` is capturing, then taken from the per-device cache.
+int noalloc_scratch(cudaStream_t st, double **out) {
   int dev = 0;
   GS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return GSYEIG_NOT_SUPPORTED;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  GS_CUDA(cudaStreamIsCapturing(st, &cap));
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[dev]) {
     void *p = nullptr;
     GS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
     g_noalloc_ptr[dev] = static_cast<double *>(p);
@@ -467,7 +471,7 @@ extern "C" int gsyeig_tridiag_eig_noalloc(const double *d, const double *e, int6
   if (dZ && (size_t)5 * (size_t)m * (size_t)cnt > kNoAllocScratchDoubles) return GSYEIG_SCRATCH_TOO_SMALL;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   double *scratch = nullptr;
-  if (dZ) GS_TRY(noalloc_scratch(&scratch));
+  if (dZ) GS_TRY(noalloc_scratch(st, &scratch));
   GS_TRY(tri_bisect(st, m, d, e, 0, nullptr, first, cnt, lam));
   // inverse iteration writes every scratch entry before reading it, so the
   // previous call's contents need no clearing

@@ -89,12 +89,15 @@ def test_sygst_matches_oracle(any_solver, n):
 
 
 @pytest.mark.parametrize("n", [1, 31, 64, 1001, 4096])
-def test_symv_matches_oracle(solver, n):
+def test_symv_matches_oracle(n):
+    """The plain FP64 ke1 product (opts.fp64_symv = 1) against a long-double host product."""
+    from paper_1111_6374_gb300 import Solver
+
     r = np.random.default_rng(n)
     M = r.standard_normal((n, n))
     C = M + M.T
     w = r.standard_normal(n)
-    z = _np(solver.symv(_cm(C), torch.from_numpy(w).cuda()))
+    z = _np(Solver(0, fp64_symv=1).symv(_cm(C), torch.from_numpy(w).cuda()))
     ref = (C.astype(np.longdouble) @ w.astype(np.longdouble)).astype(np.float64)
     # deterministic worst-case-style bound 2 n eps max|C| max|w| (real errors are far smaller)
     assert np.abs(z - ref).max() <= 2 * n * np.finfo(float).eps * np.abs(C).max() * np.abs(w).max()
@@ -384,3 +387,134 @@ def test_solve_operator_and_restart_modes(fp64_symv, qr_restart, which):
     assert info["restarts"] > 0
     w, X = _np(w), _np(X)
     _check_pairs(A, B, w, X, w_or, lam, f"fp64_symv={fp64_symv}")
+
+
+@pytest.mark.parametrize("scale_exp", [140, -140, 133, -133])
+def test_potrf_of_pencils_scaled_out_of_fp32_range(any_solver, scale_exp):
+    """B scaled by 2^+-140 (and by ~1e+-40): pivots beyond FP32's overflow
+    and subnormal thresholds.  The diagonal-block reciprocals are range
+    reduced, so U is the oracle's U scaled by 2^(e/2) on every engine."""
+    n = 700
+    B = inputs.make_pencil(n, seed=17)[1].numpy() * np.ldexp(1.0, scale_exp)
+    Uo = oracle.potrf(B)
+    dB = _cm(B)
+    assert any_solver.potrf(dB) == 0
+    U = np.triu(_np(dB))
+    assert np.isfinite(U).all()
+    assert np.abs(U - Uo).max() <= 1e-11 * np.abs(Uo).max()
+
+
+def test_solve_of_pencil_scaled_out_of_fp32_range(solver):
+    """(A 2^140, B 2^-140): eigenvalues scaled by 2^280, vectors by 2^70;
+    the oracle's pairs on both routes."""
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = 512, 10
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=19))
+    As, Bs = A * np.ldexp(1.0, 140), B * np.ldexp(1.0, -140)
+    w_or, _ = oracle.gsyeig(As, Bs, s)
+    assert np.allclose(w_or, lam[:s] * np.ldexp(1.0, 280), rtol=1e-10)
+    for inverse in (0, 1):
+        w, X, info = Solver(0, inverse=inverse).solve(torch.from_numpy(As).cuda(), torch.from_numpy(Bs).cuda(), s)
+        assert info["inverse"] == inverse
+        _check_pairs(As, Bs, _np(w), _np(X), w_or, lam, f"scaled inverse={inverse}")
+
+
+def test_inverse_route_rejects_indefinite_b():
+    """B with negative eigenvalues (B - 1.5 I, B's spectrum in ~[1, 5]): the
+    direct route's Cholesky of B fails; the inverse route, which never
+    factors B, sees a non-positive Ritz value of L^-T B L^-1 and returns
+    NOT_SPD as well instead of pairs that are not the smallest of (A, B)."""
+    from paper_1111_6374_gb300 import GsyeigError, Solver
+
+    n, s = 600, 8
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=23))
+    Bi = B - 1.5 * np.eye(n)
+    assert np.linalg.eigvalsh(Bi).min() < -0.1
+    with pytest.raises(oracle.NotSPD):
+        oracle.potrf(Bi)
+    for inverse in (0, 1):
+        with pytest.raises(GsyeigError) as ei:
+            Solver(0, inverse=inverse).solve(torch.from_numpy(A).cuda(), torch.from_numpy(Bi).cuda(), s)
+        assert ei.value.status == 1, inverse
+
+
+def test_device_wait_expiry_returns_timeout_and_next_call_succeeds():
+    """opts.wait_limit makes the bounded device-side waits in the main loops
+    of the tensor-core GEMM (potrf) and of the ke1 kernel (Lanczos) give up
+    after a few polls.  The kernels then drain their own copies and MMAs,
+    free TMEM and return; the call reports GSYEIG_TIMEOUT, and the next call
+    on a handle with the default bound gives the oracle's result."""
+    from paper_1111_6374_gb300 import GsyeigError, Solver
+
+    n = 1000
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=29))
+    Uo = oracle.potrf(B)
+    short = Solver(0, wait_limit=1)
+    with pytest.raises(GsyeigError) as ei:
+        short.potrf(_cm(B))
+    assert ei.value.status == 3
+    C = oracle.sygst(A, Uo)
+    with pytest.raises(GsyeigError) as ei:
+        short.syev_lanczos(torch.from_numpy(C).cuda(), 8)
+    assert ei.value.status == 3
+    with pytest.raises(GsyeigError) as ei:
+        short.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 8)
+    assert ei.value.status == 3
+    # the same handle with the default bound, and a fresh one
+    short.set_options(wait_limit=0)
+    for sol in (short, Solver(0)):
+        dB = _cm(B)
+        assert sol.potrf(dB) == 0
+        assert np.abs(np.triu(_np(dB)) - Uo).max() <= 1e-11 * np.abs(Uo).max()
+        w_or, _ = oracle.gsyeig(A, B, 8)
+        w, X, info = sol.solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), 8)
+        _check_pairs(A, B, _np(w), _np(X), w_or, lam, "after timeout")
+
+
+@pytest.mark.parametrize("n", [1, 63, 65, 4097, 16384])
+def test_symv_double_float_operator_matches_long_double(n):
+    """The solver's default ke1 operator (C's lower triangle as fp32 hi/lo
+    tiles, compensated fp32 products, double-float partial sums) through
+    gsyeig_symv, element by element against a long-double host product:
+    |z_i - (C w)_i| <= 64 2^-48 sum_j |c_ij| |w_j|.  C_hi + C_lo and
+    w_hi + w_lo each carry a relative error of 2^-48 per entry, and every
+    product and partial sum adds a few roundings of the same size."""
+    from paper_1111_6374_gb300 import Solver
+
+    r = np.random.default_rng(n + 1)
+    M = r.standard_normal((n, n))
+    C = M + M.T
+    C[np.arange(n), np.arange(n)] *= 0.5 ** np.arange(n)[::-1].clip(0, 30)  # a few tiny diagonal entries
+    w = r.standard_normal(n) * np.exp(r.uniform(-3, 3, n))
+    z = _np(Solver(0, fp64_symv=0).symv(_cm(C), torch.from_numpy(w).cuda()))
+    # every row up to n = 4097; at the benchmark order a seeded sample of
+    # 512 rows (long double is software arithmetic on some hosts)
+    rows = np.arange(n) if n <= 4097 else np.sort(r.choice(n, 512, replace=False))
+    Cl, wl = C[rows].astype(np.longdouble), w.astype(np.longdouble)
+    ref = Cl @ wl
+    bound = 64 * 2.0**-48 * (np.abs(Cl) @ np.abs(wl))
+    err = np.abs(z[rows].astype(np.longdouble) - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
+@pytest.mark.parametrize("n,s,inverse", [(512, 10, 0), (1000, 37, 1), (700, 12, 1), (257, 5, 0)])
+def test_solve_implicit_variant_ki_matches_oracle(n, s, inverse):
+    """Variant KI (Section 2.3, Table 1): Lanczos on U^-T G U^-1 applied
+    implicitly, C never formed; the oracle's pairs, G left as it was (lower
+    triangle mirrored), and the same Krylov dimension as KE."""
+    from paper_1111_6374_gb300 import Solver
+
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=n + 3 * s))
+    w_or, X_or = oracle.gsyeig(A, B, s)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    w, X, info = Solver(0, implicit=1, inverse=inverse).solve(dA, dB, s, overwrite=True)
+    assert info["inverse"] == inverse and info["nconv"] >= s
+    w, X = _np(w), _np(X)
+    _check_pairs(A, B, w, X, w_or, lam, f"KI n={n} inverse={inverse}")
+    cn = np.abs(lam).max()
+    ang, lim = _checks.max_subspace_angle(B, X, X_or, w, lam, cn, 1e-12 * cn)
+    assert ang <= lim, (ang, lim)
+    G = _np(dB if inverse else dA)
+    G0 = B if inverse else A
+    assert np.array_equal(G, G0), "KI must leave the untransformed matrix as it was"
