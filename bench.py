@@ -260,12 +260,14 @@ def run_ours(args, ws, rank, local):
         A.copy_(A0)
         B.copy_(B0)
 
-    def timed(sol, steps, warmup, clk=None):
+    def timed(sol, steps, warmup, profile=False):
+        """Time `steps` solves; profile=True also records CUDA events around
+        every kernel class (for the breakdown; the events cost time)."""
         for _ in range(warmup):
             restore()
             sol.solve(A, B, s, overwrite=True)
         torch.cuda.synchronize()
-        sol.set_options(profile=1)
+        sol.set_options(profile=1 if profile else 0)
         times, infos = [], []
         for _ in range(steps):
             restore()
@@ -289,12 +291,16 @@ def run_ours(args, ws, rank, local):
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        w, X, times, infos = timed(solver, args.steps, 0)
+        w, X, times, _ = timed(solver, args.steps, 0)
     torch.cuda.synchronize()
     barrier(ws)
     launches = (kernel_launches() - l_before) // max(1, args.steps)
     ms = statistics.mean(times)
     ms_all = max_over_ranks(ms, ws, dev)
+    # one more step with CUDA events around every kernel class: the breakdown
+    # and the roofline of the dominant kernel (event times of that step)
+    _, _, ptimes, infos = timed(solver, 1, 0, profile=True)
+    ms_prof = ptimes[0]
 
     # accuracy of the last timed solve against the constructed spectrum and (A, B)
     rel = float(((w - lam[:s]).abs() / lam[:s].abs()).max())
@@ -323,7 +329,7 @@ def run_ours(args, ws, rank, local):
     other = None
     if not args.no_other_route:
         osol = Solver(local, inverse=0 if args.route == "inverse" else 1)
-        _, _, ot, oi = timed(osol, max(1, min(args.steps, 2)), 1)
+        _, _, ot, oi = timed(osol, max(1, min(args.steps, 2)), 1, profile=True)
         oi = oi[-1]
         other = {"route": "direct" if args.route == "inverse" else "inverse", "inverse_used": oi["inverse"],
                  "ms_per_step": max_over_ranks(statistics.mean(ot), ws, dev), "steps": len(ot),
@@ -335,7 +341,7 @@ def run_ours(args, ws, rank, local):
     def one_solve(**opts):
         """One profiled solve of the benchmark pencil with other options (no warm-up)."""
         sol = Solver(local, **opts)
-        _, _, t, i = timed(sol, 1, 0)
+        _, _, t, i = timed(sol, 1, 0, profile=True)
         i = i[-1]
         sol.close()
         return {"ms_per_step": max_over_ranks(t[0], ws, dev), "steps": 1, "options": opts,
@@ -383,7 +389,7 @@ def run_ours(args, ws, rank, local):
                     "bound": "tensor", "achieved": 28 * c_eq, "peak": bf16, "unit": "TFLOP/s",
                     "frac": 28 * c_eq / bf16, "fp64_equivalent_tflops": c_eq,
                     "peak_source": f"{src} bf16 burst (MEASURED_PEAKS.json)",
-                    "launches_per_step": c_n, "ms_per_step": c_ms, "share_of_step": c_ms / ms,
+                    "launches_per_step": c_n, "ms_per_step": c_ms, "share_of_step": c_ms / ms_prof,
                     "ms_per_launch": c_ms / max(1.0, c_n),
                     "algorithmic_flops_per_launch": 28 * c_fl / max(1.0, c_n),
                     "slicing_ms_per_step": g_ms - c_ms}
@@ -392,7 +398,7 @@ def run_ours(args, ws, rank, local):
         gemm = {"kernel": "k_dgemm: FP64 FMA GEMM of gs1/gs2/bt1", "bound": "alu", "achieved": g_fp64eq,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": g_fp64eq / fp64_peak,
                 "peak_source": f"{src} bf16 x nominal FP64/bf16 1.25/2250"}
-    gemm.update({"launches_per_step": g_n, "ms_per_step": g_ms, "share_of_step": g_ms / ms})
+    gemm.update({"launches_per_step": g_n, "ms_per_step": g_ms, "share_of_step": g_ms / ms_prof})
     df = solver.opts.fp64_symv == 0
     sym_gbs = s_by / (s_ms * 1e-3) / 1e9 if s_ms > 0 else 0.0
     symv = {"kernel": "k_symv_df (+ split, reduce): ke1 on fp32 hi/lo triangle tiles" if df else
@@ -400,7 +406,7 @@ def run_ours(args, ws, rank, local):
             "frac": sym_gbs / hbm, "peak_source": f"{src} HBM copy (MEASURED_PEAKS.json)",
             "algorithmic_bytes_per_launch": s_by / max(1, s_n), "launches_per_step": s_n,
             "ms_per_launch": s_ms / max(1, s_n), "fp64_equivalent_tflops": s_fl / (s_ms * 1e-3) / 1e12 if s_ms else 0.0,
-            "share_of_step": s_ms / ms}
+            "share_of_step": s_ms / ms_prof}
     for k, name in ((core, "k_sliced_umma"), (symv, "k_symv_df" if df else "k_symv_cols_v2")):
         if k is None:
             continue
@@ -424,7 +430,10 @@ def run_ours(args, ws, rank, local):
                     "ms_symv": last["symv_ms"], "ms_orth": last["orth_ms"], "ms_restart": last["restart_ms"],
                     "ms_ritz": last["ritz_ms"]},
         # live per-class CUDA-event times of one step (the library stream, profile = 1)
-        "classes_ms_per_step": {"gemm_core (k_sliced_umma)": c_ms, "gemm_slicing": g_ms - c_ms,
+        "profiled_step_ms": ms_prof,
+        "classes_ms_per_step": {"gemm_core (k_sliced_umma)": c_ms,
+                                "gemm_slicing_kernels": sum(i["slice_ms"] for i in infos) / nst,
+                                "gemm_calls_other (launch gaps, copies)": g_ms - c_ms - sum(i["slice_ms"] for i in infos) / nst,
                                 "diag_blocks (k_potrf_diag + k_trtri_cols)": sum(i["diag_ms"] for i in infos) / nst,
                                 "symv (ke1)": s_ms, "orth (CGS2 + normalise)": sum(i["orth_ms"] for i in infos) / nst,
                                 "ritz": sum(i["ritz_ms"] for i in infos) / nst,

@@ -64,8 +64,9 @@ typedef struct {
   uint64_t seed;        /* seed of the counter-based start vector (default 0) */
   const double *v0;     /* optional device start vector of length n (NULL = random) */
   double timeout_ms;    /* 0 = none; checked between restarts only */
-  int32_t block;        /* panel width nb of the blocked factorisations, 16..160; 0 = default (128).  The
-                           trailing matrix gets rank-4nb updates */
+  int32_t block;        /* panel width nb of the blocked factorisations (and order of the diagonal
+                           blocks factored on one SM), 16..160; 0 = default (128).  The trailing
+                           matrix gets rank-512 updates when nb divides 512, else rank-4nb ones */
   int32_t profile;      /* 1 = time every GEMM-engine and symv launch with CUDA events on the
                            library stream and report them in gsyeig_info (small overhead) */
   int32_t fp64_gemm;    /* 0 (default): the GEMMs of gsyeig_solve (the O(n^3) ones of gs1/gs2/bt1 and the
@@ -126,6 +127,21 @@ typedef struct {
    * check_every Lanczos steps (once the projected matrix holds the kept pairs), so that a good
    * start can stop before the Krylov dimension is reached; 0 (default): at the end of a cycle only. */
   int32_t check_every;
+  /* 1: mixed precision for the Lanczos stage (the paper's operator is the per-iteration cost, Section
+   * 2.3): block Lanczos (block size 16) with C streamed as fp32 tiles and fp32 accumulation, FP64
+   * reorthogonalisation (CGS2) and projected matrix, then an FP64 block refinement (LOBPCG on the
+   * k = s + max(16, s/8) Ritz vectors, Rayleigh-Ritz on [X, R, P] with the products by C on the
+   * FP64-accurate tensor-core engine) until the s wanted residuals meet tol ||C||.  krylov_dim is the
+   * block Krylov dimension (default min(max(5s, s + 64)) rounded up to 16).  gs1, gs2 and bt1 are
+   * unchanged.  On the inverse route B's definiteness is not checked.  Not with implicit = 1. */
+  int32_t mixed;
+  /* 1: each Lanczos cycle (without check_every) is captured once into a CUDA graph and replayed
+   * while the handle's buffers and the operator stay the same: one host launch per cycle instead of
+   * about 8 per step, for the many small problems of a batch.  Ignored while profile = 1. */
+  int32_t graph;
+  /* > 0: at most this many CTAs (SMs) for the persistent tensor-core GEMM, so that the problems of a
+   * batch solved concurrently on several streams share the GPU; 0 = one CTA per SM. */
+  int32_t max_ctas;
 } gsyeig_opts;
 
 /* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
@@ -166,6 +182,10 @@ typedef struct {
   double tnorm;           /* the recurrence's running estimate of ||T|| (bounds the operator's spectrum
                              from the Krylov space: a filter_edge for a following solve) */
   int64_t filter_matvecs; /* operator applications of the start vector's Chebyshev filter */
+  double slice_ms;        /* opts.profile = 1: event time of the kernels slicing GEMM operands into digits */
+  /* opts.mixed = 1: fp32 block steps, FP64 refinement iterations and the event time of both stages */
+  int64_t block_steps, refine_iters;
+  double ms_block_lanczos, ms_refine;
 } gsyeig_info;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -260,6 +280,103 @@ int gsyeig_tridiag_eig(gsyeig_handle h, const double *d, const double *e, int64_
  * -5 cnt, -6 lam, -8 ldz. */
 int gsyeig_tridiag_eig_noalloc(const double *d, const double *e, int64_t m, int64_t first, int64_t cnt, double *lam,
                                double *dZ, int64_t ldz, void *cuda_stream);
+
+/* C = alpha op(A) op(B) + beta C (op = transpose when transA / transB is
+ * nonzero) with the GEMM engine the handle's options select (by default the
+ * FP64-accurate sliced bf16 tensor-core engine; opts.fp64_gemm = 1: FP64 FMA).
+ * op(A) is M x K, op(B) K x N, C M x N, all column-major device arrays.  The
+ * paper's route needs only its own products; this is the same engine for
+ * callers' products (e.g. the overlaps X(t+1)^T B X(t) of a warm-started
+ * sequence). */
+int gsyeig_gemm(gsyeig_handle h, int transA, int transB, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc);
+
+/* ---- learned warm start (NEXT to the paper's route) ---------------------
+ * Sequences of related problems (Section 3: the related eigenproblems of a
+ * DFT self-consistency cycle) let a small network propose the start of the
+ * next solve.  The MLP maps n_in features -> n_hidden -> n_hidden -> n_out
+ * (ReLU after the two hidden layers); n_in <= 256, n_hidden a multiple of 16
+ * up to 256, n_out <= 256.  Its parameters are fp32, packed as W1
+ * (n_hidden x n_in, row-major), b1, W2 (n_hidden x n_hidden), b2, W3 (n_out x
+ * n_hidden), b3; every product of the forward and backward pass runs on the
+ * bf16 tensor cores (operands rounded to bf16 to nearest even, fp32
+ * accumulation).  Matrices X (batch x n_in), Y, T (batch x n_out) are
+ * row-major fp32.  All pointers are device pointers; the caller provides a
+ * workspace of gsyeig_mlp_workspace_floats() floats, and the calls allocate
+ * nothing.  Calls run on `stream` (cudaStream_t, NULL = legacy default) and
+ * are synchronous on return except gsyeig_mlp_adam and the gsyeig_ws_*
+ * calls, which are only enqueued.  Negative returns name the bad argument
+ * (1-based); GSYEIG_TIMEOUT if a bounded wait for the tensor core ran out. */
+int64_t gsyeig_mlp_param_count(int32_t n_in, int32_t n_hidden, int32_t n_out);           /* -1: bad sizes */
+int64_t gsyeig_mlp_workspace_floats(int32_t n_in, int32_t n_hidden, int32_t n_out, int64_t batch);
+/* weights uniform in +-sqrt(6 / fan_in) from a counter-based generator of seed, biases 0 */
+int gsyeig_mlp_init(float *params, int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void *stream);
+/* Y = net(X), batch rows */
+int gsyeig_mlp_forward(const float *params, int32_t n_in, int32_t n_hidden, int32_t n_out, const float *X,
+                       int64_t batch, float *Y, float *ws, void *stream);
+/* Gradient (packed like the parameters) of the weighted mean squared error
+ * loss = sum_{b,o} w_o (Y - T)^2 / (2 batch) (out_weights: n_out entries, NULL
+ * = all ones), batch <= 256; *loss (device float, may be NULL) gets the loss. */
+int gsyeig_mlp_grad(const float *params, int32_t n_in, int32_t n_hidden, int32_t n_out, const float *X,
+                    const float *T, const float *out_weights, int64_t batch, float *grad, float *loss, float *ws,
+                    void *stream);
+/* One Adam step (Kingma and Ba 2015, bias-corrected; step counts from 1) on
+ * `count` parameters with moments m, v (zero before the first step). */
+int gsyeig_mlp_adam(float *params, float *m, float *v, const float *grad, int64_t count, int64_t step, float lr,
+                    float beta1, float beta2, float eps, void *stream);
+/* Features of a solved problem for its successor, from its s ascending
+ * eigenvalues theta and those of the problem before (theta_prev): with g the
+ * mean spacing of theta, f[j] = (theta[j] - theta[s-1]) / g, f[s+j] =
+ * (theta[j] - theta_prev[j]) / g, f[2s] = dt_rel (2s + 1 features);
+ * scal[0..1] (device doubles) = theta[s-1], g for decoding. */
+int gsyeig_ws_features(int64_t s, const double *theta, const double *theta_prev, double dt_rel, float *features,
+                       double *scal, void *stream);
+/* Training targets of those features from the successor's solution:
+ * t[0] = (theta_next[s-1] - scal[0]) / scal[1], t[1+j] = || P[:, j] || with P
+ * = X_next^T B X (s x s, ld ldp) the overlaps of the previous eigenvectors
+ * with the successor's, capped at 1 (s + 1 targets). */
+int gsyeig_ws_targets(int64_t s, const double *theta_next, const double *scal, const double *P, int64_t ldp,
+                      float *targets, void *stream);
+/* Network outputs (s + 1) to a warm start: weights[j] = clamp(o[1+j], wmin,
+ * 1) for opts.start_weights and *cut = scal[0] + scal[1] (o[0] + margin) for
+ * opts.filter_cut (device doubles). */
+int gsyeig_ws_decode(int64_t s, const float *outputs, const double *scal, double margin, double wmin, double *weights,
+                     double *cut, void *stream);
+
+/* ---- batches of independent problems ---------------------------------- */
+/* One problem of a batch: the arguments of gsyeig_solve (device pointers). */
+typedef struct {
+  double *A;
+  int64_t lda;
+  double *B;
+  int64_t ldb;
+  int64_t n, s;
+  int32_t which, reserved;
+  double *w;
+  double *X;
+  int64_t ldx;
+} gsyeig_problem;
+
+/* Solve `count` independent problems (device pointers; each as
+ * gsyeig_solve with the options of h) concurrently: `nstreams` (1..16)
+ * internal handles, each on its own stream and host thread, take the
+ * problems largest first from a shared queue; the tensor-core GEMM of each
+ * is capped at ceil(SMs / nstreams) CTAs (unless opts.max_ctas is set) and
+ * every Lanczos cycle is replayed from a CUDA graph (opts.graph).  The
+ * panel width of each problem comes from a built-in autotuner (when
+ * opts.block = 0): for each size class (n rounded up to a multiple of 512)
+ * it times the factorisation steps of a synthetic SPD matrix of that order
+ * for each candidate width once per handle and keeps the fastest
+ * (gsyeig_autotuned_block reports the choice).  statuses[i] and infos[i]
+ * (both may be NULL) receive each problem's outcome; the call returns
+ * GSYEIG_SUCCESS when every problem succeeded, else the first failing
+ * problem's status.  Synchronous on return. */
+int gsyeig_solve_batched(gsyeig_handle h, int64_t count, const gsyeig_problem *probs, int32_t nstreams,
+                         int32_t *statuses, gsyeig_info *infos);
+
+/* The panel width the autotuner of gsyeig_solve_batched chose for order n
+ * on this handle (tuning it now if needed); 0 on failure. */
+int32_t gsyeig_autotuned_block(gsyeig_handle h, int64_t n);
 
 /* Number of kernels this library has launched in the calling process. */
 int64_t gsyeig_kernel_launches(void);

@@ -43,7 +43,15 @@ class Opts(ctypes.Structure):
                 ("preserve_inputs", ctypes.c_int32), ("verify", ctypes.c_int32), ("implicit", ctypes.c_int32),
                 ("wait_limit", ctypes.c_int32), ("start_block", ctypes.c_void_p), ("start_weights", ctypes.c_void_p),
                 ("start_cols", ctypes.c_int64), ("ld_start", ctypes.c_int64), ("filter_cut", ctypes.c_double),
-                ("filter_edge", ctypes.c_double), ("filter_degree", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+                ("filter_edge", ctypes.c_double), ("filter_degree", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("mixed", ctypes.c_int32), ("graph", ctypes.c_int32), ("max_ctas", ctypes.c_int32)]
+
+
+class Problem(ctypes.Structure):
+    """gsyeig_problem: one problem of a batch (device pointers)."""
+    _fields_ = [("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("s", ctypes.c_int64), ("which", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("w", ctypes.c_void_p), ("X", ctypes.c_void_p), ("ldx", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -59,7 +67,9 @@ class Info(ctypes.Structure):
                [("gemm_core_launches", ctypes.c_int64)] + \
                [(f, ctypes.c_double) for f in ("gemm_core_ms", "gemm_core_flops")] + \
                [("diag_launches", ctypes.c_int64), ("diag_ms", ctypes.c_double), ("tnorm", ctypes.c_double),
-                ("filter_matvecs", ctypes.c_int64)]
+                ("filter_matvecs", ctypes.c_int64), ("slice_ms", ctypes.c_double)] + \
+               [(f, ctypes.c_int64) for f in ("block_steps", "refine_iters")] + \
+               [(f, ctypes.c_double) for f in ("ms_block_lanczos", "ms_refine")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -95,6 +105,19 @@ def load(build_if_missing: bool = True):
         "gsyeig_tridiag_eig": ([vp, vp, vp, i64, i64, i64, vp, vp, i64], i32),
         "gsyeig_kernel_launches": ([], i64),
         "gsyeig_tridiag_eig_noalloc": ([vp, vp, i64, i64, i64, vp, vp, i64, vp], i32),
+        "gsyeig_gemm": ([vp, i32, i32, i64, i64, i64, dp, vp, i64, vp, i64, dp, vp, i64], i32),
+        "gsyeig_solve_batched": ([vp, i64, vp, i32, vp, vp], i32),
+        "gsyeig_autotuned_block": ([vp, i64], i32),
+        "gsyeig_mlp_param_count": ([i32, i32, i32], i64),
+        "gsyeig_mlp_workspace_floats": ([i32, i32, i32, i64], i64),
+        "gsyeig_mlp_init": ([vp, i32, i32, i32, ctypes.c_uint64, vp], i32),
+        "gsyeig_mlp_forward": ([vp, i32, i32, i32, vp, i64, vp, vp, vp], i32),
+        "gsyeig_mlp_grad": ([vp, i32, i32, i32, vp, vp, vp, i64, vp, vp, vp, vp], i32),
+        "gsyeig_mlp_adam": ([vp, vp, vp, vp, i64, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, vp], i32),
+        "gsyeig_ws_features": ([i64, vp, vp, dp, vp, vp, vp], i32),
+        "gsyeig_ws_targets": ([i64, vp, vp, vp, i64, vp, vp], i32),
+        "gsyeig_ws_decode": ([i64, vp, vp, dp, dp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -232,6 +255,33 @@ class Solver:
         d["status"] = st
         return w, X, d
 
+    def solve_batched(self, pencils, s, which: str = "smallest", streams: int = 8, overwrite: bool = False):
+        """Independent problems [(A_i, B_i), ...] (device tensors) through
+        gsyeig_solve_batched; returns [(w_i, X_i, info_i)] in input order."""
+        probs = (Problem * len(pencils))()
+        outs, keep = [], []
+        for i, (A, B) in enumerate(pencils):
+            _check_f64(A, B)
+            if not overwrite:
+                A = A.clone(memory_format=torch.contiguous_format)
+                B = B.clone(memory_format=torch.contiguous_format)
+            n = A.shape[0]
+            si = s[i] if isinstance(s, (list, tuple)) else s
+            X = colmajor_empty(n, si, device=A.device)
+            w = torch.empty(si, device=A.device, dtype=torch.float64)
+            probs[i] = Problem(A.data_ptr(), _ld(A, True), B.data_ptr(), _ld(B, True), n, si,
+                               LARGEST if which == "largest" else SMALLEST, 0, w.data_ptr(), X.data_ptr(), X.stride(1))
+            outs.append((w, X))
+            keep.append((A, B))
+        st = (ctypes.c_int32 * len(pencils))()
+        infos = (Info * len(pencils))()
+        rc = self.lib.gsyeig_solve_batched(self._h, len(pencils), probs, streams, st, infos)
+        self._check(rc, "solve_batched")
+        return [(w, X, dict(infos[i].as_dict(), status=st[i])) for i, (w, X) in enumerate(outs)]
+
+    def autotuned_block(self, n: int) -> int:
+        return int(self.lib.gsyeig_autotuned_block(self._h, n))
+
     # -- single steps -----------------------------------------------------
     def potrf(self, B: torch.Tensor):
         """In place: U (B = U^T U) in the upper triangle of column-major B; returns 0 or failing pivot."""
@@ -276,6 +326,20 @@ class Solver:
         d = info.as_dict()
         d["status"] = st
         return w, Y, d
+
+    def gemm(self, A: torch.Tensor, B: torch.Tensor, C: torch.Tensor | None = None, transA: bool = False,
+             transB: bool = False, alpha: float = 1.0, beta: float = 0.0):
+        """C = alpha op(A) op(B) + beta C on the library's GEMM engine (column-major tensors)."""
+        _check_f64(A, B)
+        M = A.shape[1] if transA else A.shape[0]
+        K = A.shape[0] if transA else A.shape[1]
+        N = B.shape[0] if transB else B.shape[1]
+        if C is None:
+            C = colmajor_empty(M, N, device=A.device)
+        self._check(self.lib.gsyeig_gemm(self._h, int(transA), int(transB), M, N, K, alpha, A.data_ptr(),
+                                         _ld(A, False), B.data_ptr(), _ld(B, False), beta, C.data_ptr(),
+                                         _ld(C, False)), "gemm")
+        return C
 
     def tridiag_eig(self, d: torch.Tensor, e: torch.Tensor, first: int, cnt: int, vectors: bool = True):
         _check_f64(d, e)

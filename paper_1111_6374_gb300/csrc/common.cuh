@@ -56,6 +56,14 @@ cudaError_t &last_cuda_error();
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize of kernel `fn` raised to
+// `bytes` on the current device, once per (kernel, device): the attribute
+// call costs host time that launch-bound sequences of small kernels feel.
+int set_max_smem(const void *fn, int bytes);
+
+// SMs of the current device (looked up once per device)
+int num_sms_cached();
+
 // ---------------------------------------------------------------------------
 // Optional per-launch timing (opts.profile): CUDA events recorded on the
 // launching stream around each GEMM-engine / symv launch, resolved after the
@@ -72,7 +80,9 @@ enum ProfClass {
   PROF_RITZ = 4,
   PROF_GEMM_CORE = 5,
   PROF_DIAG = 6,  // the diagonal-block factor and inverse kernels of gs1
-  PROF_NCLASS = 7
+  PROF_SLICE = 7,  // the kernels slicing GEMM operands into bf16 digit planes
+  PROF_SYMV32 = 8, // the fp32 block operator of the mixed-precision stage
+  PROF_NCLASS = 9
 };
 
 struct KernelProfiler {
@@ -125,6 +135,7 @@ struct GemmContext {
   size_t ws_bytes = 0;
   int *err = nullptr;   // device flag: a bounded wait inside the tcgen05 engine expired
   uint32_t spin = 0;    // poll limit of the engine's main-loop waits (0 = the default bound)
+  int max_ctas = 0;     // > 0: cap on the persistent grid (CTAs, one per SM)
 };
 GemmContext *&current_gemm();
 
@@ -132,7 +143,7 @@ size_t umma_workspace_bytes(int64_t M, int64_t N, int64_t K);
 int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
               const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
               TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err,
-              uint32_t spin);
+              uint32_t spin, int max_ctas);
 
 size_t sliced_workspace_bytes(int64_t M, int64_t N, int64_t K);
 int sliced_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
@@ -159,7 +170,15 @@ struct FactorWork {
   size_t panel_elems = 0;
   int *flag = nullptr;      // device int: first failed pivot (1-based) or 0
   double *rdiag = nullptr;  // device, nb entries: 1 / U(i, i) of the diagonal block just factored
+  // inverses of the NB x NB outer diagonal blocks of U (NB = outer_block(nb), ld NB, zeros below the
+  // diagonal) and a staging buffer of NB x max(n, s) doubles for the outer panels
+  double *UinvO = nullptr;
+  double *panelO = nullptr;
+  bool outer_ready = false;  // UinvO holds the current factor's outer inverses
 };
+
+// order NB of the outer blocks of the blocked factorisations for inner width nb
+int64_t outer_block(int nb);
 
 int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, FactorWork &w);
 int trtri_diag_blocks(cudaStream_t st, int64_t n, const double *U, int64_t ldu, int nb, double *Uinv);

@@ -182,20 +182,44 @@ int trtri_diag_blocks(cudaStream_t st, int64_t n, const double *U, int64_t ldu, 
   return GSYEIG_SUCCESS;
 }
 
-// Two-level blocking: inner steps of nb (the diagonal-block kernels and the
-// panels) and outer blocks of NB = kOuter nb.  Within an outer block the
-// inner rank-nb updates touch only the rest of the outer block; the trailing
-// matrix beyond it receives one rank-NB update per outer block, so the
-// GEMM engine's per-element epilogue is paid once per NB columns of K
-// instead of once per nb.
+// Two-level blocking: inner steps of nb (the diagonal-block kernels, one
+// CTA each) and outer blocks of NB = outer_block(nb) (512 when nb divides
+// it, else kOuter nb).  The inner steps stay inside an outer diagonal block;
+// everything beyond it goes through the inverse U_JJ^-1 of the whole outer
+// block, so that each outer block costs one GEMM with K = NB per pass
+// instead of several narrow ones (each GEMM call slices its operands into
+// digit planes, a cost proportional to the operand, not to K).
 constexpr int kOuter = 4;
 
+int64_t outer_block(int nb) { return (512 % nb == 0) ? 512 : (int64_t)kOuter * nb; }
+
+namespace {
+
+// U_JJ^-1 of the outer diagonal block J (order jb, starting at J0) into
+// w.UinvO, from the inverses of its nb x nb blocks (already in w.Uinv).
+int outer_inverse(cudaStream_t st, int64_t J0, int64_t jb, const double *U, int64_t ldu, int nb, FactorWork &w) {
+  const int64_t NB = outer_block(nb);
+  FactorWork wj = w;
+  wj.Uinv = w.Uinv + (size_t)(J0 / nb) * nb * nb;
+  return trtri_upper_blocked(st, jb, &U[GS_IDX(J0, J0, ldu)], ldu, w.UinvO + (size_t)(J0 / NB) * NB * NB, NB, nb, wj,
+                             true);
+}
+
+}  // namespace
+
+// Right-looking blocked Cholesky in two levels: inner steps of nb (the
+// diagonal kernels, the panel U_k,rest = U_kk^-T B_k,rest over the whole
+// rest of the row, and the update of the rows of the outer block below the
+// step), and one rank-NB update of the trailing matrix per outer block.
+// The panels use the nb x nb inverses only (explicit inverses of whole
+// outer blocks would cost backward stability on badly scaled matrices).
 int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, FactorWork &w) {
   size_t sm = diag_smem_bytes(nb);
   GS_TRY(set_smem((const void *)k_potrf_diag, sm));
   GS_TRY(set_smem((const void *)k_trtri_cols, sm));
   GS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
-  const int64_t NB = (int64_t)kOuter * nb;
+  w.outer_ready = false;
+  const int64_t NB = outer_block(nb);
   for (int64_t J0 = 0; J0 < n; J0 += NB) {
     const int64_t J1 = std::min(n, J0 + NB);
     for (int64_t k0 = J0; k0 < J1; k0 += nb) {
@@ -231,50 +255,50 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
   return GSYEIG_SUCCESS;
 }
 
+// The outer-block inverses U_JJ^-1 of every outer block (have_uinv: the
+// nb x nb inverses are in w.Uinv already).
+int outer_inverses(cudaStream_t st, int64_t n, const double *U, int64_t ldu, int nb, FactorWork &w, bool have_uinv) {
+  if (!have_uinv) GS_TRY(trtri_diag_blocks(st, n, U, ldu, nb, w.Uinv));
+  const int64_t NB = outer_block(nb);
+  for (int64_t J0 = 0; J0 < n; J0 += NB) GS_TRY(outer_inverse(st, J0, std::min(n, J0 + NB) - J0, U, ldu, nb, w));
+  w.outer_ready = true;
+  return GSYEIG_SUCCESS;
+}
+
+// sygst: C = U^-T A U^-1, lower triangle, then mirrored.  With the outer
+// inverses U_JJ^-1 (formed here from the nb x nb ones) every step is one
+// GEMM per outer block and pass with K = NB.
 int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *U, int64_t ldu, int nb,
                   FactorWork &w, bool have_uinv) {
   GS_TRY(symmetrize(st, n, A, lda, true));
-  if (!have_uinv) GS_TRY(trtri_diag_blocks(st, n, U, ldu, nb, w.Uinv));
-  const int64_t NB = (int64_t)kOuter * nb;
-  // Step 1: W = U^-T A, block row by block row (forward substitution).
+  if (!have_uinv || !w.outer_ready) GS_TRY(outer_inverses(st, n, U, ldu, nb, w, have_uinv));
+  const int64_t NB = outer_block(nb);
+  // Step 1: W = U^-T A, block row by block row: W_J = U_JJ^-T A_J, then the
+  // rows below, A_rest -= U_J,rest^T W_J
   for (int64_t J0 = 0; J0 < n; J0 += NB) {
-    const int64_t J1 = std::min(n, J0 + NB);
-    for (int64_t k0 = J0; k0 < J1; k0 += nb) {
-      const int kb = (int)std::min<int64_t>(nb, J1 - k0);
-      const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
-      double *Ak = &A[GS_IDX(k0, 0, lda)];
-      GS_TRY(dgemm(st, true, false, kb, n, kb, 1.0, Uinv_k, nb, Ak, lda, 0.0, w.panel, kb));
-      GS_TRY(copy_block(st, kb, n, w.panel, kb, Ak, lda));
-      const int64_t rin = J1 - k0 - kb;  // rows of the outer block below this step
-      if (rin > 0)
-        GS_TRY(dgemm(st, true, false, rin, n, kb, -1.0, &U[GS_IDX(k0, k0 + kb, ldu)], ldu, w.panel, kb, 1.0,
-                     &A[GS_IDX(k0 + kb, 0, lda)], lda));
-    }
-    const int64_t r2 = n - J1;  // rows beyond the outer block: one rank-NB update
+    const int64_t J1 = std::min(n, J0 + NB), jb = J1 - J0;
+    const double *UiJ = w.UinvO + (size_t)(J0 / NB) * NB * NB;
+    double *AJ = &A[GS_IDX(J0, 0, lda)];
+    GS_TRY(dgemm(st, true, false, jb, n, jb, 1.0, UiJ, NB, AJ, lda, 0.0, w.panelO, jb));
+    GS_TRY(copy_block(st, jb, n, w.panelO, jb, AJ, lda));
+    const int64_t r2 = n - J1;
     if (r2 > 0)
-      GS_TRY(dgemm(st, true, false, r2, n, J1 - J0, -1.0, &U[GS_IDX(J0, J1, ldu)], ldu, &A[GS_IDX(J0, 0, lda)], lda,
-                   1.0, &A[GS_IDX(J1, 0, lda)], lda));
+      GS_TRY(dgemm(st, true, false, r2, n, jb, -1.0, &U[GS_IDX(J0, J1, ldu)], ldu, AJ, lda, 1.0,
+                   &A[GS_IDX(J1, 0, lda)], lda));
   }
-  // Step 2: lower triangle of C = W U^-1, block column by block column.
+  // Step 2: lower triangle of C = W U^-1, block column by block column:
+  // C_{J0:, J} = W_{J0:, J} U_JJ^-1 (rows above the diagonal of the block
+  // are not needed), then C_rest,rest (lower) -= C_rest,J U_J,rest
   for (int64_t J0 = 0; J0 < n; J0 += NB) {
-    const int64_t J1 = std::min(n, J0 + NB);
-    for (int64_t k0 = J0; k0 < J1; k0 += nb) {
-      const int kb = (int)std::min<int64_t>(nb, J1 - k0);
-      const int64_t rows = n - k0;
-      const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
-      double *Ck = &A[GS_IDX(k0, k0, lda)];
-      GS_TRY(dgemm(st, false, false, rows, kb, kb, 1.0, Ck, lda, Uinv_k, nb, 0.0, w.panel, rows));
-      GS_TRY(copy_block(st, rows, kb, w.panel, rows, Ck, lda));
-      const int64_t rest = n - k0 - kb;
-      const int64_t cin = J1 - k0 - kb;  // columns of the outer block right of this step
-      if (cin > 0)
-        GS_TRY(dgemm(st, false, false, rest, cin, kb, -1.0, &w.panel[kb], rows, &U[GS_IDX(k0, k0 + kb, ldu)], ldu,
-                     1.0, &A[GS_IDX(k0 + kb, k0 + kb, lda)], lda, TRI_LOWER, 0));
-    }
-    const int64_t r2 = n - J1;  // lower trailing matrix beyond the outer block: one rank-NB update
+    const int64_t J1 = std::min(n, J0 + NB), jb = J1 - J0, rows = n - J0;
+    const double *UiJ = w.UinvO + (size_t)(J0 / NB) * NB * NB;
+    double *CJ = &A[GS_IDX(J0, J0, lda)];
+    GS_TRY(dgemm(st, false, false, rows, jb, jb, 1.0, CJ, lda, UiJ, NB, 0.0, w.panelO, rows));
+    GS_TRY(copy_block(st, rows, jb, w.panelO, rows, CJ, lda));
+    const int64_t r2 = n - J1;
     if (r2 > 0)
-      GS_TRY(dgemm(st, false, false, r2, r2, J1 - J0, -1.0, &A[GS_IDX(J1, J0, lda)], lda, &U[GS_IDX(J0, J1, ldu)],
-                   ldu, 1.0, &A[GS_IDX(J1, J1, lda)], lda, TRI_LOWER, 0));
+      GS_TRY(dgemm(st, false, false, r2, r2, jb, -1.0, &A[GS_IDX(J1, J0, lda)], lda, &U[GS_IDX(J0, J1, ldu)], ldu,
+                   1.0, &A[GS_IDX(J1, J1, lda)], lda, TRI_LOWER, 0));
   }
   GS_TRY(symmetrize(st, n, A, lda, true));
   return GSYEIG_SUCCESS;
@@ -303,18 +327,21 @@ int trtri_upper_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu
   return GSYEIG_SUCCESS;
 }
 
+// bt1: Y <- U^-1 Y by backward block substitution over the outer blocks,
+// Y_J = U_JJ^-1 Y_J, then the rows above, Y_top -= U_top,J Y_J.
 int trsm_back_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu, double *Y, int64_t ldy, int64_t s,
                       int nb, FactorWork &w, bool have_uinv) {
-  if (!have_uinv) GS_TRY(trtri_diag_blocks(st, n, U, ldu, nb, w.Uinv));
-  const int64_t last = ((n - 1) / nb) * nb;
-  for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
-    const int kb = (int)std::min<int64_t>(nb, n - k0);
-    const double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
-    double *Yk = &Y[GS_IDX(k0, 0, ldy)];
-    GS_TRY(dgemm(st, false, false, kb, s, kb, 1.0, Uinv_k, nb, Yk, ldy, 0.0, w.panel, kb));
-    GS_TRY(copy_block(st, kb, s, w.panel, kb, Yk, ldy));
-    if (k0 > 0)
-      GS_TRY(dgemm(st, false, false, k0, s, kb, -1.0, &U[GS_IDX(0, k0, ldu)], ldu, w.panel, kb, 1.0, Y, ldy));
+  if (!have_uinv || !w.outer_ready) GS_TRY(outer_inverses(st, n, U, ldu, nb, w, have_uinv));
+  const int64_t NB = outer_block(nb);
+  const int64_t last = ((n - 1) / NB) * NB;
+  for (int64_t J0 = last; J0 >= 0; J0 -= NB) {
+    const int64_t jb = std::min(NB, n - J0);
+    const double *UiJ = w.UinvO + (size_t)(J0 / NB) * NB * NB;
+    double *YJ = &Y[GS_IDX(J0, 0, ldy)];
+    GS_TRY(dgemm(st, false, false, jb, s, jb, 1.0, UiJ, NB, YJ, ldy, 0.0, w.panelO, jb));
+    GS_TRY(copy_block(st, jb, s, w.panelO, jb, YJ, ldy));
+    if (J0 > 0)
+      GS_TRY(dgemm(st, false, false, J0, s, jb, -1.0, &U[GS_IDX(0, J0, ldu)], ldu, w.panelO, jb, 1.0, Y, ldy));
   }
   return GSYEIG_SUCCESS;
 }

@@ -9,6 +9,8 @@
 // 4 x 4 register block per thread, 16-deep K slices staged through shared
 // memory.  At two FMAs per SM-clock a K slice takes ~32k cycles, so global
 // load latency (~1k cycles) needs no multi-stage pipeline.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace gs {
@@ -18,6 +20,23 @@ std::atomic<int64_t> g_launches{0};
 cudaError_t &last_cuda_error() {
   static thread_local cudaError_t e = cudaSuccess;
   return e;
+}
+
+int set_max_smem(const void *fn, int bytes) {
+  struct Key {
+    const void *fn;
+    int dev, bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Key> done;
+  int dev = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Key &k : done)
+    if (k.fn == fn && k.dev == dev && k.bytes >= bytes) return GSYEIG_SUCCESS;
+  GS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.push_back({fn, dev, bytes});
+  return GSYEIG_SUCCESS;
 }
 
 KernelProfiler *&current_profiler() {
@@ -241,7 +260,7 @@ int dgemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64
         const double bk = (k0 == 0) ? beta : 1.0;
         if (gc->umma)
           GS_TRY(umma_gemm(st, transA, transB, M, N, kc, alpha, Ak, lda, Bk, ldb, bk, C, ldc, mode, diag, abort_flag,
-                           gc->ws, gc->ws_bytes, gc->err, gc->spin));
+                           gc->ws, gc->ws_bytes, gc->err, gc->spin, gc->max_ctas));
         else
           GS_TRY(sliced_gemm(st, transA, transB, M, N, kc, alpha, Ak, lda, Bk, ldb, bk, C, ldc, mode, diag, abort_flag,
                              gc->ws, gc->ws_bytes));

@@ -28,7 +28,7 @@
 // accuracy in small products.  The solver exposes opts.fp64_gemm = 1 for
 // such inputs.
 //
-// Kernels: k_row_exp (per-row exponent), k_split (digits, written K-major
+// Kernels: k_inner_exp2 / k_rowsplit2 (exponents and digits, written K-major
 // as bf16 slices padded to 64 rows x 32 k), k_sliced_gemm (mma.sync bf16 ->
 // fp32 on 64 x 64 output tiles, 8 warps, 7 level accumulators per warp).
 #include <cuda_bf16.h>
@@ -196,14 +196,10 @@ int sliced_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N,
   P.Kpad = Kpad;
   P.SA = static_cast<unsigned char *>(ws);
   P.SB = P.SA + (size_t)S * Mpad * Kpad * 2;
-  P.ea = reinterpret_cast<int *>(P.SB + (size_t)S * Npad * Kpad * 2);
-  P.eb = P.ea + Mpad;
-  P.kA = P.eb + Npad;
-  P.kB = P.kA + Kpad;
-  P.ksh = P.kB + Kpad;
+  slicing::slice_layout(P, reinterpret_cast<int *>(P.SB + (size_t)S * Npad * Kpad * 2));
   GS_TRY(slicing::slice_operands(st, transA, transB, M, N, K, A, lda, B, ldb, P, {false, 0}, {false, 0}));
   const size_t smem = (size_t)NSTAGE * STAGE_BYTES;
-  GS_CUDA(cudaFuncSetAttribute((const void *)k_sliced_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GS_TRY(set_max_smem((const void *)k_sliced_gemm, (int)smem));
   dim3 grid((unsigned)(Mpad / TM), (unsigned)(Npad / TN));
   k_sliced_gemm<<<grid, GEMM_THREADS, smem, st>>>(M, N, Mpad, Npad, Kpad, reinterpret_cast<__nv_bfloat16 *>(P.SA),
                                                   reinterpret_cast<__nv_bfloat16 *>(P.SB), P.ea, P.eb, alpha, beta, C,

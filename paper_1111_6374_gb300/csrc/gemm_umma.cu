@@ -3,7 +3,7 @@
 // how the 28 digit-pair products are issued and how the exact level sums are
 // turned into FP64).
 //
-//  * Operands are pre-split by k_split straight into the UMMA
+//  * Operands are pre-split by k_rowsplit2 straight into the UMMA
 //    "no-swizzle K-major" core-matrix layout (8 rows x 16 bytes per core
 //    matrix, K-adjacent cores 128 B apart, row-adjacent cores 256 B apart),
 //    grouped so that one K stage (32 k: two k16 blocks of all 7 slices) of a
@@ -51,12 +51,7 @@ constexpr int UMMA_MAX_K = 512;
 constexpr int TMEM_COLS = 512;
 constexpr uint32_t SPIN_LIMIT = 1u << 24;
 
-int num_sms() {
-  int dev = 0, n = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  return n > 0 ? n : 1;
-}
+int num_sms() { return num_sms_cached(); }
 
 // ---------------------------------------------------------------- PTX -----
 __device__ __forceinline__ uint32_t sptr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -75,6 +70,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
   const uint32_t a = sptr(bar);
   for (uint32_t it = 0; it < limit; it++) {
     uint32_t done;
+    if (limit < SPIN_LIMIT) {
+      // a test limit: poll without the hardware's suspended wait, so that
+      // the limit counts polls and the wait can run out
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(a), "r"(parity)
+          : "memory");
+      if (done) return true;
+      continue;
+    }
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -533,7 +539,7 @@ size_t umma_workspace_bytes(int64_t M, int64_t N, int64_t K) {
 int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K, double alpha,
               const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
               TriMode mode, int64_t diag, const int *abort_flag, void *ws, size_t ws_bytes, int *err,
-              uint32_t spin) {
+              uint32_t spin, int max_ctas) {
   if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
   if (K > UMMA_MAX_K || K <= 0) return GSYEIG_NOT_SUPPORTED;
   const int64_t Mpad = ceil_div(M, UM) * UM, Npad = ceil_div(N, UN) * UN, Kpad = ceil_div(K, KPAD) * KPAD;
@@ -544,18 +550,15 @@ int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, i
   P.Kpad = Kpad;
   P.SA = static_cast<unsigned char *>(ws);
   P.SB = P.SA + (size_t)S * Mpad * Kpad * 2;
-  P.ea = reinterpret_cast<int *>(P.SB + (size_t)S * Npad * Kpad * 2);
-  P.eb = P.ea + Mpad;
-  P.kA = P.eb + Npad;
-  P.kB = P.kA + Kpad;
-  P.ksh = P.kB + Kpad;
+  slicing::slice_layout(P, reinterpret_cast<int *>(P.SB + (size_t)S * Npad * Kpad * 2));
   GS_TRY(slicing::slice_operands(st, transA, transB, M, N, K, A, lda, B, ldb, P, {true, UM}, {true, UN}));
   const size_t smem = (size_t)NBUF * (A_STAGE + B_STAGE) + 128;
-  GS_CUDA(cudaFuncSetAttribute((const void *)k_sliced_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GS_TRY(set_max_smem((const void *)k_sliced_umma, (int)smem));
   TileGrid g{M, N, diag, (int)(Mpad / UM), (int)(Npad / UN), (int)mode};
   // CTAs without an active tile (TRI modes) only set up and leave
   const int64_t tiles = (int64_t)g.mt * g.nt;
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, num_sms());
+  const int64_t ctas = max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms();
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, ctas);
   KernelProfiler *prof = current_profiler();
   const size_t e0 = prof ? prof->start(st) : SIZE_MAX;
   k_sliced_umma<<<grid, UMMA_THREADS, smem, st>>>(g, Kpad / UKS, P.SA, P.SB, P.ea, P.eb, alpha, beta, C, ldc,

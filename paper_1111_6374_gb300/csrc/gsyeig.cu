@@ -3,12 +3,18 @@
 // Device memory for inputs/outputs belongs to the caller; the handle owns a
 // grow-on-demand workspace.  The driver only sequences kernels and reads
 // back a few scalars per restart (converged count, breakdown flag).
+#include <algorithm>
+#include <array>
 #include <chrono>
+#include <map>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <new>
 
 #include "lanczos.cuh"
+#include "mixed.cuh"
 #include "symv_df.cuh"
 
 namespace gs {
@@ -50,6 +56,7 @@ struct gsyeig_ctx {
   gsyeig_opts opts{};
   // workspace
   DevBuf uinv, panel, flag, diag;
+  DevBuf uinvO;           // inverses of the outer diagonal blocks and the outer panel staging
   DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts, arrow;
   DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
   DevBuf pA, pB;          // working copies when opts.preserve_inputs
@@ -60,11 +67,25 @@ struct gsyeig_ctx {
   DevBuf kinv, dfopL, kt; // variant KI: U^-1, the tiles of L = U^-T, two temporaries
   DevBuf tmin;            // smallest eigenvalue of the final projected matrix
   DevBuf wstart;          // start-block construction and Chebyshev filter vectors
+  // mixed precision: fp32 operator and staging, block basis, projected matrices, refinement blocks
+  DevBuf mx_op, mx_w, mx_z, mx_V, mx_Zd, mx_H, mx_part, mx_T, mx_small, mx_Sb, mx_CSb, mx_tmp, mx_fw, mx_P;
   DfOperator op, opL;
   bool use_df = false;
   bool ki = false;        // the operator is U^-T G U^-1 applied implicitly (variant KI)
   KernelProfiler prof;
   GemmContext gemm;
+  // opts.graph: instantiated graphs of Lanczos cycles, keyed by everything the captured launches use
+  struct CycleGraph {
+    std::array<uintptr_t, 12> key{};
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;
+  };
+  CycleGraph graphs[4];
+  int graph_next = 0;
+  // gsyeig_solve_batched: internal handles and the autotuned panel width per size class
+  std::vector<gsyeig_ctx *> subs;
+  std::map<int64_t, int> tuned;
+  std::mutex tune_mu;
 };
 
 namespace {
@@ -101,6 +122,7 @@ struct ProfScope {
     info->gemm_core_flops = fl[PROF_GEMM_CORE];
     info->diag_launches = l[PROF_DIAG];
     info->diag_ms = ms[PROF_DIAG];
+    info->slice_ms = ms[PROF_SLICE];
   }
   ~ProfScope() {
     if (on) {
@@ -140,7 +162,7 @@ int nb_of(gsyeig_handle h, int64_t n) {
 }
 
 // Install the GEMM mode for this call; the sliced GEMM needs slices of two
-// operands of at most max(n, s) rows and K up to the outer block 4 nb (the
+// operands of at most max(n, s) rows and K up to the outer block (the
 // tcgen05 engine takes up to 512 per call).
 int gemm_setup(gsyeig_handle h, int64_t n, int nb, int64_t s) {
   h->gemm.sliced = (h->opts.fp64_gemm != 1);
@@ -148,7 +170,7 @@ int gemm_setup(gsyeig_handle h, int64_t n, int nb, int64_t s) {
   if (h->gemm.sliced) {
     const int64_t r = std::max<int64_t>(n, s);
     GS_TRY(h->gemm_ws.ensure(
-        std::max(sliced_workspace_bytes(r, r, nb), umma_workspace_bytes(r, r, std::min<int64_t>(512, 4 * (int64_t)nb)))));
+        std::max(sliced_workspace_bytes(r, r, nb), umma_workspace_bytes(r, r, 512))));
     h->gemm.ws = h->gemm_ws.p;
     h->gemm.ws_bytes = h->gemm_ws.bytes;
     GS_TRY(h->gemm_err.ensure(64));
@@ -156,6 +178,7 @@ int gemm_setup(gsyeig_handle h, int64_t n, int nb, int64_t s) {
     GS_CUDA(cudaMemsetAsync(h->gemm.err, 0, sizeof(int), h->st));  // cudaMalloc does not zero
   }
   h->gemm.spin = (uint32_t)h->opts.wait_limit;
+  h->gemm.max_ctas = h->opts.max_ctas;
   current_gemm() = &h->gemm;
   return GSYEIG_SUCCESS;
 }
@@ -180,6 +203,10 @@ struct GemmScope {
 int factor_ws(gsyeig_handle h, int64_t n, int nb, int64_t s, FactorWork &w) {
   GS_TRY(gemm_setup(h, n, nb, s));
   const int64_t nblk = ceil_div(n, nb);
+  const int64_t NB = outer_block(nb), nout = ceil_div(n, NB);
+  GS_TRY(h->uinvO.ensure(((size_t)nout * NB * NB + (size_t)NB * std::max<int64_t>(n, s)) * sizeof(double)));
+  w.UinvO = h->uinvO.d();
+  w.panelO = w.UinvO + (size_t)nout * NB * NB;
   GS_TRY(h->uinv.ensure((size_t)nblk * nb * nb * sizeof(double)));
   GS_TRY(h->panel.ensure((size_t)std::max<int64_t>(n, s) * nb * sizeof(double) + 64));
   GS_TRY(h->flag.ensure(256 + 160 * sizeof(double)));
@@ -247,6 +274,55 @@ int lanczos_step(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t m, int64_t
   GS_TRY(lz_finalize(st, j, m, h->h1.d(), h->h2.d(), h->sq.d(), lz_nparts(n), h->alpha.d(), h->beta.d(),
                      static_cast<LanczosState *>(h->state.p)));
   GS_TRY(lz_scale_into(st, n, z, V + (size_t)(j + 1) * n, static_cast<LanczosState *>(h->state.p)));
+  return GSYEIG_SUCCESS;
+}
+
+// Steps j0..m-1 of a Lanczos cycle.  With opts.graph (and no profiler) the
+// cycle's launches are captured once into a CUDA graph, kept while every
+// buffer, size and operator it touches stays the same, and replayed: a
+// cycle of m steps is one launch from the host instead of about 8 m.
+int lanczos_cycle(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t m, int64_t j0, const double *C, int64_t ldc) {
+  if (h->opts.graph != 1 || current_profiler()) {
+    for (int64_t j = j0; j < m; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
+    return GSYEIG_SUCCESS;
+  }
+  const std::array<uintptr_t, 12> key = {
+      (uintptr_t)h->V.p, (uintptr_t)h->z.p, (uintptr_t)h->h1.p, (uintptr_t)h->state.p, (uintptr_t)C,
+      (uintptr_t)ldc, (uintptr_t)n, (uintptr_t)m, (uintptr_t)j0,
+      (uintptr_t)(h->use_df ? h->op.hi : nullptr) ^ (uintptr_t)(h->ki ? h->opL.hi : nullptr) ^ (uintptr_t)h->ki,
+      (uintptr_t)h->dfpart.p ^ (uintptr_t)h->kt.p, (uintptr_t)h->alpha.p ^ ((uintptr_t)h->beta.p << 1) ^ (uintptr_t)h->sq.p};
+  gsyeig_ctx::CycleGraph *g = nullptr;
+  for (auto &c : h->graphs)
+    if (c.exec && c.key == key) g = &c;
+  if (!g) {
+    g = &h->graphs[h->graph_next];
+    h->graph_next = (h->graph_next + 1) % 4;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+    const int64_t l0 = g_launches.load();
+    GS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    int rc = GSYEIG_SUCCESS;
+    for (int64_t j = j0; j < m && rc == GSYEIG_SUCCESS; j++) rc = lanczos_step(h, st, n, m, j, C, ldc);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    g->nodes = g_launches.load() - l0;
+    g_launches.fetch_sub(g->nodes);  // captured, not launched
+    if (rc != GSYEIG_SUCCESS || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != GSYEIG_SUCCESS ? rc : GSYEIG_CUDA_ERROR;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      g->exec = nullptr;
+      cudaGetLastError();
+      return GSYEIG_CUDA_ERROR;
+    }
+    g->key = key;
+  }
+  GS_CUDA(cudaGraphLaunch(g->exec, st));
+  count_launch(g->nodes);
   return GSYEIG_SUCCESS;
 }
 
@@ -426,7 +502,12 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
         jend = std::min(std::max(jend, j + 1), m);
       }
       const int64_t jb = j;
-      for (; j < jend; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
+      if (ce == 0) {
+        GS_TRY(lanczos_cycle(h, st, n, m, j, C, ldc));
+        j = jend;
+      } else {
+        for (; j < jend; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
+      }
       matvecs += jend - jb;
       if (jend == m) break;
       // an early convergence test on the leading jend x jend matrix
@@ -449,6 +530,7 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
     if (stop_pass) {
       // finish the cycle's bookkeeping the same way as a full pass: the steps
       // after a breakdown were no-ops
+      matvecs += m - j;
       for (; j < m; j++) GS_TRY(lanczos_step(h, st, n, m, j, C, ldc));
     }
     GS_CUDA(cudaMemcpyAsync(&hs, dstate, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -545,6 +627,317 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
   return status;
 }
 
+
+// ---- mixed precision (fp32 block Lanczos, FP64 block refinement) ----------
+
+// cnt eigenpairs (the cnt smallest or largest, ascending) of a small dense
+// symmetric H (m x m, ld m, device): Lanczos with full reorthogonalisation
+// over the whole space (m steps, the tridiagonalisation Householder would
+// give up to rounding) and the Ritz solve of T_m, on the handle's own
+// kernels with the FP64 product.  th (cnt) and Z (m x cnt, ld ldz), device.
+int small_syev(gsyeig_handle h, const double *H, int64_t m, int64_t cnt, int which, double *th, double *Z,
+               int64_t ldz) {
+  if (cnt < 1 || cnt >= m) return GSYEIG_NOT_SUPPORTED;
+  const gsyeig_opts saved = h->opts;
+  KernelProfiler *prof = current_profiler();
+  GemmContext *gc = current_gemm();
+  current_profiler() = nullptr;
+  current_gemm() = nullptr;
+  gsyeig_opts &o = h->opts;
+  o.krylov_dim = m;
+  o.keep = 0;
+  o.fp64_symv = 1;
+  o.qr_restart = 0;
+  o.check_every = 0;
+  o.start_block = nullptr;
+  o.v0 = nullptr;
+  o.filter_degree = 0;
+  o.max_restarts = 4;
+  o.timeout_ms = 0;
+  const int st = lanczos_run(h, H, m, m, cnt, which, th, Z, ldz, nullptr, nullptr);
+  h->opts = saved;
+  current_profiler() = prof;
+  current_gemm() = gc;
+  return st;
+}
+
+// A small factorisation workspace (the solve's own diagonal-block inverses
+// stay intact for bt1).
+struct SmallFactor {
+  FactorWork w;
+  double *G, *Rinv, *R1, *R2, *norms;
+};
+
+int small_factor(gsyeig_handle h, int64_t bmax, SmallFactor &f) {
+  const int nb = 128;
+  const int64_t nblk = ceil_div(bmax, nb);
+  const int64_t NB = outer_block(nb), nout = ceil_div(bmax, NB);
+  const size_t need = (size_t)nblk * nb * nb + (size_t)bmax * nb + 4 * (size_t)bmax * bmax + (size_t)bmax + 512 +
+                      (size_t)nout * NB * NB + (size_t)NB * bmax;
+  GS_TRY(h->mx_fw.ensure(need * sizeof(double)));
+  double *p = h->mx_fw.d();
+  f.w.UinvO = p;
+  p += (size_t)nout * NB * NB;
+  f.w.panelO = p;
+  p += (size_t)NB * bmax;
+  f.w.Uinv = p;
+  p += (size_t)nblk * nb * nb;
+  f.w.panel = p;
+  p += (size_t)bmax * nb;
+  f.G = p;
+  p += (size_t)bmax * bmax;
+  f.Rinv = p;
+  p += (size_t)bmax * bmax;
+  f.R1 = p;
+  p += (size_t)bmax * bmax;
+  f.R2 = p;
+  p += (size_t)bmax * bmax;
+  f.norms = p;
+  p += bmax;
+  f.w.flag = reinterpret_cast<int *>(p);
+  f.w.rdiag = p + 32;
+  return GSYEIG_SUCCESS;
+}
+
+// Orthonormalise the n x b block Z (ld ldz) by Cholesky QR twice: G = Z^T Z
+// = R^T R, Z <- Z R^-1, twice (the products on the GEMM engine in use, or
+// the FP64 tall-skinny kernels for b <= 16).  The same right factors are
+// applied to CZ (if not NULL), so that CZ stays C Z.  With Rout != NULL,
+// Rout (b x b, ld b) = R2 R1 (Z_in = Z_out Rout).  Returns GSYEIG_NOT_SPD if
+// a Gram matrix is not numerically positive definite (Z rank deficient).
+int cholqr2(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t b, double *Z, int64_t ldz, double *CZ, int64_t ldcz,
+            double *Rout, SmallFactor &f, double *tmp, double *part) {
+  const int nb = (int)std::min<int64_t>(128, b);
+  for (int pass = 0; pass < 2; pass++) {
+    if (b <= 16)
+      GS_TRY(ts_dots(st, n, b, (int)b, Z, ldz, Z, ldz, part, f.G, b));
+    else
+      GS_TRY(dgemm(st, true, false, b, b, n, 1.0, Z, ldz, Z, ldz, 0.0, f.G, b));
+    GS_TRY(potrf_blocked(st, b, f.G, b, nb, f.w));
+    int flag = 0;
+    GS_CUDA(cudaMemcpyAsync(&flag, f.w.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (flag) return GSYEIG_NOT_SPD;
+    GS_TRY(trtri_upper_blocked(st, b, f.G, b, f.Rinv, b, nb, f.w, true));
+    GS_TRY(dgemm(st, false, false, n, b, b, 1.0, Z, ldz, f.Rinv, b, 0.0, tmp, n));
+    GS_TRY(copy_block(st, n, b, tmp, n, Z, ldz));
+    if (CZ) {
+      GS_TRY(dgemm(st, false, false, n, b, b, 1.0, CZ, ldcz, f.Rinv, b, 0.0, tmp, n));
+      GS_TRY(copy_block(st, n, b, tmp, n, CZ, ldcz));
+    }
+    // the factor is the upper triangle of G (its strict lower triangle still holds Gram entries)
+    if (Rout) GS_TRY(copy_upper(st, b, f.G, b, pass == 0 ? f.R1 : f.R2, b));
+  }
+  if (Rout) GS_TRY(dgemm(st, false, false, b, b, b, 1.0, f.R2, b, f.R1, b, 0.0, Rout, b));
+  return GSYEIG_SUCCESS;
+}
+
+// Lanczos stage of the mixed-precision route (C full symmetric, FP64):
+// block Lanczos (b = 16) with C streamed as fp32 tiles and fp32
+// accumulation, the reorthogonalisation (CGS2) and the projected band
+// matrix in FP64; the k = s + guard Ritz vectors of that stage then go
+// through an FP64 block refinement (LOBPCG: Rayleigh-Ritz on [X, R, P],
+// C products on the FP64-accurate GEMM engine) until the s wanted residuals
+// meet tol ||C||.  Ritz values ascending into theta_out, vectors into Y.
+int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_t s, int which, double *theta_out,
+                  double *Y, int64_t ldy, gsyeig_info *info, double *ms_ke3) {
+  cudaStream_t st = h->st;
+  constexpr int BK = 16;
+  int64_t mb = h->opts.krylov_dim > 0 ? h->opts.krylov_dim : std::max<int64_t>(5 * s, s + 64);
+  mb = std::min<int64_t>(ceil_div(mb, BK) * BK, (n / BK) * BK - BK);
+  const int64_t g = std::max<int64_t>(16, s / 8);
+  const int64_t k = std::min<int64_t>(s + g, mb - BK);
+  if (n < 8 * BK || mb < 2 * BK || s >= k || 3 * k >= n) return GSYEIG_NOT_SUPPORTED;
+  const int64_t nblk = mb / BK;
+  // ---- workspace
+  GS_TRY(h->mx_op.ensure(f32_operator_bytes(n)));
+  GS_TRY(h->mx_w.ensure(f32_block_bytes(n)));
+  GS_TRY(h->mx_z.ensure(f32_block_bytes(n)));
+  GS_TRY(h->mx_V.ensure((size_t)n * (mb + BK) * sizeof(double)));
+  GS_TRY(h->mx_Zd.ensure((size_t)n * BK * sizeof(double)));
+  GS_TRY(h->mx_H.ensure((size_t)2 * (mb + BK) * BK * sizeof(double)));
+  GS_TRY(h->mx_part.ensure(ts_part_doubles(n, mb + BK) * sizeof(double)));
+  GS_TRY(h->mx_T.ensure((size_t)mb * mb * sizeof(double) + 64));
+  const int64_t zrows = std::max<int64_t>(mb, 3 * k);
+  GS_TRY(h->mx_small.ensure(((size_t)9 * k * k + (size_t)zrows * k + 5 * k + 64) * sizeof(double)));
+  GS_TRY(h->mx_Sb.ensure((size_t)n * 3 * k * sizeof(double)));
+  GS_TRY(h->mx_CSb.ensure((size_t)n * 3 * k * sizeof(double)));
+  GS_TRY(h->mx_tmp.ensure((size_t)n * 4 * k * sizeof(double)));
+  GS_TRY(h->mx_P.ensure((size_t)n * 2 * k * sizeof(double)));
+  SmallFactor sf;
+  GS_TRY(small_factor(h, 2 * k, sf));
+  F32Operator op;
+  op.tiles = static_cast<float *>(h->mx_op.p);
+  op.W = static_cast<float *>(h->mx_w.p);
+  op.Z = static_cast<float *>(h->mx_z.p);
+  double *V = h->mx_V.d(), *Zd = h->mx_Zd.d(), *H1 = h->mx_H.d(), *H2 = H1 + (mb + BK) * BK;
+  double *part = h->mx_part.d(), *T = h->mx_T.d(), *cn = T + (size_t)mb * mb;
+  double *Hs = h->mx_small.d(), *Zs = Hs + 9 * k * k, *thv = Zs + zrows * k, *res = thv + 3 * k;
+  double *Sb = h->mx_Sb.d(), *CSb = h->mx_CSb.d(), *tmp = h->mx_tmp.d();
+  GemmContext *gc = current_gemm();  // the FP64-accurate engine of the solve
+  cudaEvent_t ev0, ev1, ev2;
+  GS_CUDA(cudaEventCreate(&ev0));
+  GS_CUDA(cudaEventCreate(&ev1));
+  GS_CUDA(cudaEventCreate(&ev2));
+  struct EvGuard {
+    cudaEvent_t a, b, c;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaEventDestroy(c);
+    }
+  } evg{ev0, ev1, ev2};
+  GS_CUDA(cudaEventRecord(ev0, st));
+  // ---- fp32 operator and a random orthonormal start block
+  GS_TRY(f32_operator_build(st, n, C, ldc, op));
+  for (int c = 0; c < BK; c++) GS_TRY(lz_random(st, n, h->opts.seed, 2000 + (uint64_t)c, V + (size_t)c * n));
+  GS_CUDA(cudaMemsetAsync(T, 0, (size_t)mb * mb * sizeof(double), st));
+  current_gemm() = nullptr;  // small products in FP64
+  int rc = cholqr2(h, st, n, BK, V, n, nullptr, 0, nullptr, sf, tmp, part);
+  if (rc != GSYEIG_SUCCESS) {
+    current_gemm() = gc;
+    return rc;
+  }
+  // ---- block Lanczos: Z = C V_j (fp32), CGS2 in FP64, Z = V_{j+1} B_j
+  int64_t blocks = 0;
+  for (int64_t j = 0; j < nblk; j++) {
+    double *Vj = V + (size_t)j * BK * n;
+    GS_TRY(f32_symm(st, op, Vj, n, Zd, n));
+    blocks++;
+    const int64_t w = (j + 1) * BK;
+    {
+      ProfRegion pr(st, PROF_ORTH);
+      GS_TRY(ts_dots(st, n, w, BK, V, n, Zd, n, part, H1, w));
+      GS_TRY(ts_update(st, n, w, BK, V, n, H1, w, Zd, n));
+      GS_TRY(ts_dots(st, n, w, BK, V, n, Zd, n, part, H2, w));
+      GS_TRY(ts_update(st, n, w, BK, V, n, H2, w, Zd, n));
+      GS_TRY(put_sum(st, BK, H1 + j * BK, H2 + j * BK, w, T, mb, j * BK));
+      if (j + 1 < nblk) {
+        double *R = Hs;  // 16 x 16
+        rc = cholqr2(h, st, n, BK, Zd, n, nullptr, 0, R, sf, tmp, part);
+        if (rc != GSYEIG_SUCCESS) {
+          current_gemm() = gc;
+          return rc == GSYEIG_NOT_SPD ? GSYEIG_NO_CONVERGENCE : rc;
+        }
+        GS_TRY(copy_block(st, n, BK, Zd, n, V + (size_t)(j + 1) * BK * n, n));
+        GS_TRY(put_block(st, BK, R, BK, T, mb, (j + 1) * BK, j * BK, true));
+      }
+    }
+  }
+  GS_TRY(sym_avg(st, mb, T, mb));
+  GS_TRY(inf_norm(st, mb, T, mb, cn));
+  double cnorm = 0.0;
+  GS_CUDA(cudaMemcpyAsync(&cnorm, cn, sizeof(double), cudaMemcpyDeviceToHost, st));
+  // ---- the k wanted Ritz pairs of the band matrix, X = V S
+  {
+    ProfRegion pr(st, PROF_RITZ);
+    GS_TRY(small_syev(h, T, mb, k, which, thv, Zs, mb));
+  }
+  current_gemm() = gc;
+  GS_TRY(dgemm(st, false, false, n, k, mb, 1.0, V, n, Zs, mb, 0.0, Sb, n));
+  GS_CUDA(cudaEventRecord(ev1, st));
+  // ---- FP64 block refinement on C (LOBPCG with soft locking: columns whose
+  // residual already meets the tolerance leave the search space, so that
+  // the normalised search directions never magnify rounding)
+  double *X = Sb, *CX = CSb, *Pb = h->mx_P.d(), *CPb = Pb + (size_t)n * k;
+  int *idx = reinterpret_cast<int *>(res + k);
+  GS_TRY(dgemm(st, false, false, n, k, n, 1.0, C, ldc, X, n, 0.0, CX, n));
+  GS_TRY(column_dots(st, n, k, X, n, CX, n, thv));  // Rayleigh quotients of the columns
+  const int64_t w0 = (which == GSYEIG_LARGEST) ? k - s : 0;  // wanted columns w0..w0+s-1
+  const double tol = h->opts.tol;
+  std::vector<double> hres(k);
+  std::vector<int> act;
+  int64_t iters = 0, products = k;
+  bool have_p = false, done = false;
+  for (; iters < 60; iters++) {
+    double *Rf = tmp;  // the k residuals
+    GS_TRY(block_resid(st, n, k, CX, X, n, thv, Rf));
+    GS_TRY(col_norms(st, n, k, Rf, n, res));
+    GS_CUDA(cudaMemcpyAsync(hres.data(), res, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (int64_t i = w0; i < w0 + s; i++) mx = std::max(mx, hres[i]);
+    if (mx <= tol * cnorm) {
+      done = true;
+      break;
+    }
+    act.clear();
+    for (int64_t i = 0; i < k; i++)
+      if (hres[i] > tol * cnorm) act.push_back((int)i);
+    const int64_t na = (int64_t)act.size();
+    ProfRegion pr(st, PROF_RESTART);
+    GS_CUDA(cudaMemcpyAsync(idx, act.data(), (size_t)na * sizeof(int), cudaMemcpyHostToDevice, st));
+    double *W = Sb + (size_t)k * n, *CW = CSb + (size_t)k * n;
+    int64_t wb = 0;
+    rc = GSYEIG_NOT_SPD;
+    for (int attempt = 0; attempt < 2 && rc != GSYEIG_SUCCESS; attempt++) {
+      if (attempt == 1) {
+        if (!have_p) break;
+        have_p = false;  // [R, P] numerically dependent: restart the directions from R
+      }
+      GS_TRY(gather_cols(st, n, na, idx, Rf, n, W, n));
+      GS_TRY(dgemm(st, false, false, n, na, n, 1.0, C, ldc, W, n, 0.0, CW, n));
+      products += na;
+      wb = na;
+      if (have_p) {
+        GS_TRY(copy_block(st, n, k, Pb, n, W + (size_t)na * n, n));
+        GS_TRY(copy_block(st, n, k, CPb, n, CW + (size_t)na * n, n));
+        wb += k;
+      }
+      // W against X (twice), C W following the same combinations
+      for (int pass = 0; pass < 2; pass++) {
+        GS_TRY(dgemm(st, true, false, k, wb, n, 1.0, X, n, W, n, 0.0, Hs, k));
+        GS_TRY(dgemm(st, false, false, n, wb, k, -1.0, X, n, Hs, k, 1.0, W, n));
+        GS_TRY(dgemm(st, false, false, n, wb, k, -1.0, CX, n, Hs, k, 1.0, CW, n));
+      }
+      GS_TRY(col_norms(st, n, wb, W, n, sf.norms));
+      GS_TRY(scale_cols(st, n, wb, W, n, sf.norms));
+      GS_TRY(scale_cols(st, n, wb, CW, n, sf.norms));
+      rc = cholqr2(h, st, n, wb, W, n, CW, n, nullptr, sf, tmp + (size_t)k * n, part);
+      if (rc != GSYEIG_SUCCESS && rc != GSYEIG_NOT_SPD) return rc;
+    }
+    if (rc != GSYEIG_SUCCESS) break;  // no new directions: keep the current pairs
+    // Rayleigh-Ritz on S = [X, W]
+    const int64_t ms = k + wb;
+    GS_TRY(dgemm(st, true, false, ms, ms, n, 1.0, Sb, n, CSb, n, 0.0, Hs, ms));
+    GS_TRY(sym_avg(st, ms, Hs, ms));
+    GS_TRY(small_syev(h, Hs, ms, k, which, thv, Zs, ms));
+    // X <- S Z, C X <- C S Z, P <- W Z_W, C P <- C W Z_W
+    double *Xn = tmp, *Pn = tmp + (size_t)k * n, *CXn = tmp + (size_t)2 * k * n, *CPn = tmp + (size_t)3 * k * n;
+    GS_TRY(dgemm(st, false, false, n, k, ms, 1.0, Sb, n, Zs, ms, 0.0, Xn, n));
+    GS_TRY(dgemm(st, false, false, n, k, ms, 1.0, CSb, n, Zs, ms, 0.0, CXn, n));
+    GS_TRY(dgemm(st, false, false, n, k, wb, 1.0, W, n, Zs + k, ms, 0.0, Pn, n));
+    GS_TRY(dgemm(st, false, false, n, k, wb, 1.0, CW, n, Zs + k, ms, 0.0, CPn, n));
+    GS_TRY(copy_block(st, n, k, Xn, n, X, n));
+    GS_TRY(copy_block(st, n, k, CXn, n, CX, n));
+    GS_TRY(copy_block(st, n, k, Pn, n, Pb, n));
+    GS_TRY(copy_block(st, n, k, CPn, n, CPb, n));
+    have_p = true;
+  }
+  // ke3: the s wanted pairs
+  GS_CUDA(cudaEventRecord(ev2, st));
+  GS_TRY(copy_block(st, n, s, X + (size_t)w0 * n, n, Y, ldy));
+  GS_CUDA(cudaMemcpyAsync(theta_out, thv + w0, (size_t)s * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  if (ms_ke3) *ms_ke3 = 0.0;
+  if (info) {
+    info->nconv = done ? s : 0;
+    info->restarts = 0;
+    info->matvecs = blocks * BK + products;
+    info->krylov_dim = mb;
+    info->keep = k;
+    info->block_steps = blocks;
+    info->refine_iters = iters;
+    info->ms_block_lanczos = elapsed(ev0, ev1);
+    info->ms_refine = elapsed(ev1, ev2);
+    info->tnorm = cnorm;
+    double mx = 0.0;
+    for (int64_t i = w0; i < w0 + s; i++) mx = std::max(mx, hres[i]);
+    info->max_ritz_estimate = cnorm > 0 ? mx / cnorm : mx;
+  }
+  return done ? GSYEIG_SUCCESS : GSYEIG_NO_CONVERGENCE;
+}
+
 int check_solve_args(int64_t lda, int64_t ldb, int64_t n, int64_t s, int which, const void *A, const void *B,
                      const void *w, const void *X, int64_t ldx) {
   if (!A) return -2;
@@ -605,11 +998,15 @@ int gsyeig_destroy(gsyeig_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
-  DevBuf *bufs[] = {&h->wstart, &h->kinv, &h->dfopL, &h->kt, &h->tmin, &h->pA, &h->pB, &h->vA, &h->vB, &h->vws, &h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
+  DevBuf *bufs[] = {&h->uinvO, &h->mx_P, &h->mx_op, &h->mx_w, &h->mx_z, &h->mx_V, &h->mx_Zd, &h->mx_H, &h->mx_part, &h->mx_T,
+                    &h->mx_small, &h->mx_Sb, &h->mx_CSb, &h->mx_tmp, &h->mx_fw, &h->wstart, &h->kinv, &h->dfopL, &h->kt, &h->tmin, &h->pA, &h->pB, &h->vA, &h->vB, &h->vws, &h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
                     &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
                     &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
   for (DevBuf *b : bufs) b->release();
   h->prof.release();
+  for (auto &g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (gsyeig_ctx *sub : h->subs) gsyeig_destroy(sub);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->st) cudaStreamDestroy(h->st);
@@ -627,7 +1024,8 @@ int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
       o->preserve_inputs > 1 || o->verify < 0 || o->verify > 1 || o->implicit < 0 || o->implicit > 1 ||
       o->wait_limit < 0 || o->filter_degree < 0 || o->filter_degree > 64 || o->check_every < 0 ||
       o->start_cols < 0 || (o->start_block && o->start_cols > 0 && o->ld_start < 1) ||
-      (o->filter_degree > 0 && !(o->filter_cut != o->filter_edge)))
+      (o->filter_degree > 0 && !(o->filter_cut != o->filter_edge)) || o->mixed < 0 || o->mixed > 1 ||
+      o->graph < 0 || o->graph > 1 || o->max_ctas < 0)
     return -2;
   if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
   h->opts = *o;
@@ -733,6 +1131,27 @@ int gsyeig_trsm_back(gsyeig_handle h, const double *dU, int64_t ldu, int64_t n, 
   FactorWork w;
   GS_TRY(factor_ws(h, n, nb, s, w));
   GS_TRY(trsm_back_blocked(h->st, n, dU, ldu, dY, ldy, s, nb, w, false));
+  GS_TRY(finish(h));
+  return gemm_check(h);
+}
+
+int gsyeig_gemm(gsyeig_handle h, int transA, int transB, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc) {
+  if (!h) return -1;
+  if (M < 0) return -4;
+  if (N < 0) return -5;
+  if (K < 0) return -6;
+  if (!A && M > 0 && K > 0) return -8;
+  if (lda < std::max<int64_t>(1, transA ? K : M)) return -9;
+  if (!B && N > 0 && K > 0) return -10;
+  if (ldb < std::max<int64_t>(1, transB ? N : K)) return -11;
+  if (!C && M > 0 && N > 0) return -13;
+  if (ldc < std::max<int64_t>(1, M)) return -14;
+  if (M == 0 || N == 0) return GSYEIG_SUCCESS;
+  GS_TRY(begin(h));
+  GemmScope gscope;
+  GS_TRY(gemm_setup(h, std::max(M, N), 128, 1));  // K = 0 scales C by beta in the FP64 kernel
+  GS_TRY(dgemm(h->st, transA != 0, transB != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc));
   GS_TRY(finish(h));
   return gemm_check(h);
 }
@@ -904,6 +1323,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   }
   const bool ki = h->opts.implicit == 1;
   if (ki && h->opts.fp64_symv == 1) return GSYEIG_NOT_SUPPORTED;  // KI runs on the double-float tiles
+  if (ki && h->opts.mixed == 1) return GSYEIG_NOT_SUPPORTED;
   if (!ki) {
     // gs2: C = U^-T G U^-1 over G (diagonal-block inverses reused from gs1)
     GS_TRY(sygst_blocked(st, n, dG, dldg, dF, dldf, nb, fw, true));
@@ -921,8 +1341,15 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   // eigenvalue of L^-T B L^-1 from above: if it is not positive, B is not
   // positive definite (the direct route's Cholesky of B would fail).
   double ms_ke3 = 0, theta_min = 1.0;
-  int status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
-                           ki ? h->kinv.d() : nullptr, inv ? &theta_min : nullptr);
+  int status;
+  if (h->opts.mixed == 1) {
+    // fp32 block Lanczos + FP64 block refinement; B's definiteness is not
+    // checked here on the inverse route
+    status = lanczos_mixed(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3);
+  } else {
+    status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
+                         ki ? h->kinv.d() : nullptr, inv ? &theta_min : nullptr, dF, dldf);
+  }
   if (status != GSYEIG_SUCCESS && status != GSYEIG_NO_CONVERGENCE && status != GSYEIG_TIMEOUT) return status;
   if (inv && !(theta_min > 0.0)) {
     if (info) info->inverse = 1;
@@ -973,3 +1400,138 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
 }
 
 }  // extern "C"
+
+// ---- batches ---------------------------------------------------------------
+
+namespace {
+
+__global__ void k_tune_matrix(int64_t n, double *M) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    const uint64_t a = (uint64_t)std::min(i, j) * 0x9E3779B97F4A7C15ull ^ (uint64_t)std::max(i, j) * 0xBF58476D1CE4E5B9ull;
+    M[idx] = (i == j) ? (double)n : (double)((a >> 11) & 0xFFFFF) * 0x1p-20 - 0.5;
+  }
+}
+
+// Time gs1 + gs2 of a synthetic diagonally dominant SPD pencil of order n
+// with each candidate panel width; the fastest wins.
+int autotune(gsyeig_handle h, int64_t n) {
+  const int cand[] = {64, 128};
+  GS_TRY(h->pA.ensure((size_t)n * n * sizeof(double)));
+  GS_TRY(h->pB.ensure((size_t)n * n * sizeof(double)));
+  cudaStream_t st = h->st;
+  float best_ms = 1e30f;
+  int best = 128;
+  const gsyeig_opts saved = h->opts;
+  for (int rep = 0; rep < 2; rep++)  // the first pass warms the workspace up
+    for (int nb : cand) {
+      if (nb > n) continue;
+      h->opts.block = nb;
+      FactorWork fw;
+      GS_TRY(factor_ws(h, n, nb, 1, fw));
+      const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096);
+      k_tune_matrix<<<g, 256, 0, st>>>(n, h->pA.d());
+      k_tune_matrix<<<g, 256, 0, st>>>(n, h->pB.d());
+      count_launch(2);
+      GS_CHECK_LAUNCH();
+      GS_CUDA(cudaEventRecord(h->ev[1], st));
+      GS_TRY(potrf_blocked(st, n, h->pB.d(), n, nb, fw));
+      GS_TRY(sygst_blocked(st, n, h->pA.d(), n, h->pB.d(), n, nb, fw, true));
+      GS_CUDA(cudaEventRecord(h->ev[2], st));
+      GS_CUDA(cudaEventSynchronize(h->ev[2]));
+      const float ms = elapsed(h->ev[1], h->ev[2]);
+      if (rep == 1 && ms < best_ms) {
+        best_ms = ms;
+        best = nb;
+      }
+    }
+  current_gemm() = nullptr;
+  h->opts = saved;
+  return best;
+}
+
+int tuned_block(gsyeig_handle h, gsyeig_handle worker, int64_t n) {
+  const int64_t cls = ceil_div(n, 512) * 512;
+  {
+    std::lock_guard<std::mutex> lock(h->tune_mu);
+    auto it = h->tuned.find(cls);
+    if (it != h->tuned.end()) return it->second;
+  }
+  const int nb = autotune(worker, cls);
+  std::lock_guard<std::mutex> lock(h->tune_mu);
+  h->tuned[cls] = nb;
+  return nb;
+}
+
+}  // namespace
+
+extern "C" int gsyeig_solve_batched(gsyeig_handle h, int64_t count, const gsyeig_problem *probs, int32_t nstreams,
+                                    int32_t *statuses, gsyeig_info *infos) {
+  if (!h) return -1;
+  if (count < 0) return -2;
+  if (!probs && count > 0) return -3;
+  if (nstreams < 1 || nstreams > 16) return -4;
+  for (int64_t i = 0; i < count; i++) {
+    const gsyeig_problem &p = probs[i];
+    if (check_solve_args(p.lda, p.ldb, p.n, p.s, p.which, p.A, p.B, p.w, p.X, p.ldx) != 0) return -3;
+  }
+  if (count == 0) return GSYEIG_SUCCESS;
+  GS_TRY(begin(h));
+  while ((int)h->subs.size() < nstreams) {
+    gsyeig_handle sub = nullptr;
+    GS_TRY(gsyeig_create(&sub, h->device, h->st));  // ordered after the caller's stream through h->st
+    h->subs.push_back(sub);
+  }
+  gsyeig_opts o = h->opts;
+  o.graph = 1;
+  o.profile = 0;
+  if (o.max_ctas == 0) o.max_ctas = (int32_t)ceil_div(num_sms_cached(), nstreams);
+  // largest problems first
+  std::vector<int64_t> order((size_t)count);
+  for (int64_t i = 0; i < count; i++) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return probs[a].n > probs[b].n; });
+  std::atomic<int64_t> next{0};
+  std::vector<int> st((size_t)count, GSYEIG_SUCCESS);
+  auto work = [&](int t) {
+    gsyeig_handle sub = h->subs[(size_t)t];
+    cudaSetDevice(h->device);
+    for (;;) {
+      const int64_t q = next.fetch_add(1);
+      if (q >= count) break;
+      const int64_t i = order[(size_t)q];
+      const gsyeig_problem &p = probs[i];
+      gsyeig_opts oi = o;
+      if (h->opts.block == 0) oi.block = tuned_block(h, sub, p.n);
+      sub->opts = oi;
+      gsyeig_info inf;
+      st[(size_t)i] = gsyeig_solve(sub, p.A, p.lda, p.B, p.ldb, p.n, p.s, p.which, p.w, p.X, p.ldx, &inf);
+      if (infos) infos[i] = inf;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nstreams; t++) pool.emplace_back(work, t);
+  work(0);
+  for (auto &th : pool) th.join();
+  int rc = GSYEIG_SUCCESS;
+  for (int64_t i = 0; i < count; i++) {
+    if (statuses) statuses[i] = st[(size_t)i];
+    if (rc == GSYEIG_SUCCESS && st[(size_t)i] != GSYEIG_SUCCESS) rc = st[(size_t)i];
+  }
+  // the caller's stream orders after every internal stream
+  for (gsyeig_handle sub : h->subs) {
+    GS_CUDA(cudaEventRecord(sub->ev[8], sub->st));
+    GS_CUDA(cudaStreamWaitEvent(h->user, sub->ev[8], 0));
+  }
+  return rc;
+}
+
+extern "C" int32_t gsyeig_autotuned_block(gsyeig_handle h, int64_t n) {
+  if (!h || n < 1) return 0;
+  if (begin(h) != GSYEIG_SUCCESS) return 0;
+  if (h->subs.empty()) {
+    gsyeig_handle sub = nullptr;
+    if (gsyeig_create(&sub, h->device, h->st) != GSYEIG_SUCCESS) return 0;
+    h->subs.push_back(sub);
+  }
+  return tuned_block(h, h->subs[0], n);
+}

@@ -59,14 +59,22 @@ __device__ __forceinline__ size_t digit_off(const DigitLayout &L, int p, int64_t
   return ((size_t)(blk * nks + ks) * S + p) * k16bytes + (size_t)mi * 256 + ki * 128 + rr * 16 + kc * 2;
 }
 
-__global__ void k_fill(int n, int *p, int v) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
-}
+// Per-k maxima kA[k] (over the rows of op(A)) and kB[k] (over the columns of
+// op(B)) in one launch: blockIdx.z selects the operand.  kA, kB start at the
+// memset sentinel KNONE (below every exponent bound).
+constexpr int KNONE = (int)0x80808080;
 
-// per-k maximum exponent of op(X) (R x K) over its rows, by atomicMax
-__global__ void k_inner_exp(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld, bool kcontig,
-                            int *__restrict__ ek) {
+__global__ void k_inner_exp2(int64_t M, int64_t N, int64_t K, const double *__restrict__ A, int64_t lda, bool a_kc,
+                             const double *__restrict__ B, int64_t ldb, bool b_kc, int *__restrict__ kA,
+                             int *__restrict__ kB) {
+  const bool isB = blockIdx.z != 0;
+  const int64_t R = isB ? N : M;
   const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  if (r0 >= R) return;
+  const double *X = isB ? B : A;
+  const int64_t ld = isB ? ldb : lda;
+  const bool kcontig = isB ? b_kc : a_kc;
+  int *ek = isB ? kB : kA;
   __shared__ int sm[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int j = ty; j < 32; j += 8) {
@@ -83,51 +91,100 @@ __global__ void k_inner_exp(int64_t R, int64_t K, const double *__restrict__ X, 
   }
 }
 
-__global__ void k_kshift(int64_t K, const int *__restrict__ ea, const int *__restrict__ eb, int *__restrict__ sh) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
-    int s = 0;
-    if (ea[k] != EXP_NONE && eb[k] != EXP_NONE) {
-      const int d = eb[k] - ea[k];
-      s = (d >= 0) ? d / 2 : -((-d + 1) / 2);
-      s = max(-SHIFT_MAX, min(SHIFT_MAX, s));
-    }
-    sh[k] = s;
-  }
+// the equalising shift s_k of column k (0 when either side is all zeros)
+__device__ __forceinline__ int kshift_of(const int *kA, const int *kB, int64_t k) {
+  const int a = kA[k], b = kB[k];
+  if (a == KNONE || b == KNONE) return 0;
+  const int d = b - a;
+  const int sft = (d >= 0) ? d / 2 : -((-d + 1) / 2);
+  return max(-SHIFT_MAX, min(SHIFT_MAX, sft));
 }
 
-// row exponents of op(X) * 2^{sgn s_k}: e_r = 1 + max_k (exp_bound + sgn s_k)
-__global__ void k_row_exp(int64_t R, int64_t K, const double *__restrict__ X, int64_t ld, bool kcontig,
-                          const int *__restrict__ kshift, int sgn, int *__restrict__ ex) {
-  const int64_t r0 = (int64_t)blockIdx.x * 32;
-  __shared__ int sm[32][33];
-  int best = EXP_NONE;
+// Raw row maxima rX[r] = max over k of (exp_bound(v_rk) + sgn s_k), by
+// atomicMax over K chunks of 128: grid (rows / 32, K / 128, operand).
+// kA == nullptr: no equalising shift (a symmetric rank-K update).
+__global__ void k_rowmax2(int64_t M, int64_t N, int64_t K, const double *__restrict__ A, int64_t lda, bool a_kc,
+                          const double *__restrict__ B, int64_t ldb, bool b_kc, const int *__restrict__ kA,
+                          const int *__restrict__ kB, int *__restrict__ rA, int *__restrict__ rB) {
+  const bool isB = blockIdx.z != 0;
+  const int64_t R = isB ? N : M;
+  const int64_t r0 = (int64_t)blockIdx.x * 32, kc0 = (int64_t)blockIdx.y * 128;
+  if (r0 >= R) return;
+  const double *X = isB ? B : A;
+  const int64_t ld = isB ? ldb : lda;
+  const bool kcontig = isB ? b_kc : a_kc;
+  const int sgn = isB ? -1 : 1;
+  int *rx = isB ? rB : rA;
+  __shared__ int red[8][33];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int64_t k0 = 0; k0 < K; k0 += 32) {
-    for (int j = ty; j < 32; j += 8) {
-      int64_t r = kcontig ? r0 + j : r0 + tx, k = kcontig ? k0 + tx : k0 + j;
-      int e = EXP_NONE;
-      if (r < R && k < K) {
-        e = exp_bound(opx(X, ld, kcontig, r, k));
-        if (e != EXP_NONE && kshift) e += sgn * kshift[k];
+  if (kcontig) {
+    // a warp per row (rows r0 + ty + 8 i), lanes along k: coalesced
+    for (int i = 0; i < 4; i++) {
+      const int64_t r = r0 + ty + 8 * i;
+      int best = EXP_NONE;
+      if (r < R)
+        for (int64_t k = kc0 + tx; k < kc0 + 128 && k < K; k += 32) {
+          int e = exp_bound(X[k + r * ld]);
+          if (e != EXP_NONE && kA) e += sgn * kshift_of(kA, kB, k);
+          best = max(best, e);
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+      if (tx == 0 && r < R && best != EXP_NONE) atomicMax(&rx[r], best);
+    }
+  } else {
+    // lanes along rows (coalesced), the 8 warps split the k chunk
+    const int64_t r = r0 + tx;
+    int best = EXP_NONE;
+    if (r < R)
+      for (int64_t k = kc0 + ty; k < kc0 + 128 && k < K; k += 8) {
+        int e = exp_bound(X[r + k * ld]);
+        if (e != EXP_NONE && kA) e += sgn * kshift_of(kA, kB, k);
+        best = max(best, e);
       }
-      if (kcontig) sm[j][tx] = e; else sm[tx][j] = e;
+    red[ty][tx] = best;
+    __syncthreads();
+    if (ty == 0) {
+      for (int j = 1; j < 8; j++) best = max(best, red[j][tx]);
+      if (r < R && best != EXP_NONE) atomicMax(&rx[r], best);
     }
-    __syncthreads();
-    if (ty == 0)
-      for (int j = 0; j < 32; j++) best = max(best, sm[tx][j]);
-    __syncthreads();
   }
-  if (ty == 0 && r0 + tx < R) ex[r0 + tx] = (best == EXP_NONE) ? EXP_NONE : best + 1;
 }
 
-// Digits of row r of op(X) * 2^{sgn s_k}, scaled by 2^{-e_r}: X = round(|v| 2^{56 - e_r + sgn s_k})
-// written as balanced base-256 digits (d_0 in [0, 128], others in [-128, 127]) times sign(v).
-__global__ void k_split(int64_t R, int64_t K, int64_t Rpad, int64_t Kpad, const double *__restrict__ X, int64_t ld,
-                        bool kcontig, const int *__restrict__ kshift, int sgn, const int *__restrict__ ex,
-                        DigitLayout L, unsigned char *__restrict__ dst) {
-  __shared__ double tile[32][33];
+// Digits of a 32 x 32 tile of one operand (grid (rows / 32, Kpad / 32,
+// operand)): entry v of row r becomes X = round(|v| 2^{56 - e_r + sgn s_k})
+// with e_r = 1 + rX[r], written as balanced base-256 digits (d_0 in
+// [0, 128], the others in [-128, 127]) times sign(v); rows R..Rpad-1 and
+// columns K..Kpad-1 are zeros.  The CTAs of the first K tile also store
+// the final row exponents e_r (EXP_NONE for a zero row).
+__global__ void k_split2(int64_t M, int64_t N, int64_t K, int64_t Mpad, int64_t Npad, int64_t Kpad,
+                         const double *__restrict__ A, int64_t lda, bool a_kc, const double *__restrict__ B,
+                         int64_t ldb, bool b_kc, const int *__restrict__ kA, const int *__restrict__ kB,
+                         const int *__restrict__ rA, const int *__restrict__ rB, int *__restrict__ ea,
+                         int *__restrict__ eb, DigitLayout LA, DigitLayout LB, unsigned char *__restrict__ SA,
+                         unsigned char *__restrict__ SB) {
+  const bool isB = blockIdx.z != 0;
+  const int64_t R = isB ? N : M, Rpad = isB ? Npad : Mpad;
   const int64_t r0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  if (r0 >= Rpad) return;
+  const double *X = isB ? B : A;
+  const int64_t ld = isB ? ldb : lda;
+  const bool kcontig = isB ? b_kc : a_kc;
+  const int sgn = isB ? -1 : 1;
+  const int *rx = isB ? rB : rA;
+  int *ex = isB ? eb : ea;
+  const DigitLayout L = isB ? LB : LA;
+  unsigned char *dst = isB ? SB : SA;
+  __shared__ double tile[32][33];
+  __shared__ int rowe[32];
   const int tx = threadIdx.x, ty = threadIdx.y;
+  if (ty == 0) {
+    const int64_t r = r0 + tx;
+    const int raw = (r < R) ? rx[r] : KNONE;
+    const int e = (raw == KNONE) ? EXP_NONE : raw + 1;
+    rowe[tx] = e;
+    if (blockIdx.y == 0 && r < R) ex[r] = e;
+  }
   for (int j = ty; j < 32; j += 8) {
     int64_t r = kcontig ? r0 + j : r0 + tx, k = kcontig ? k0 + tx : k0 + j;
     double v = 0.0;
@@ -139,7 +196,7 @@ __global__ void k_split(int64_t R, int64_t K, int64_t Rpad, int64_t Kpad, const 
     const int64_t r = r0 + j, k = k0 + tx;
     if (r >= Rpad || k >= Kpad) continue;
     const double v = tile[j][tx];
-    const int e = (r < R) ? ex[r] : EXP_NONE;
+    const int e = rowe[j];
     uint64_t Xm = 0;
     bool neg = false;
     if (v != 0.0 && e != EXP_NONE) {
@@ -149,7 +206,7 @@ __global__ void k_split(int64_t R, int64_t K, int64_t Rpad, int64_t Kpad, const 
       uint64_t m = u & ((1ull << 52) - 1);
       int Eeff = E;
       if (E != 0) m |= (1ull << 52); else Eeff = 1;
-      const int ks = (kshift && k < K) ? sgn * kshift[k] : 0;
+      const int ks = (kA && k < K) ? sgn * kshift_of(kA, kB, k) : 0;
       const int sh = Eeff - 1019 - e + ks;  // |v 2^ks| 2^{56 - e} = m 2^sh <= 2^55
       if (sh >= 0) Xm = m << sh;
       else if (sh > -60) Xm = (m + (1ull << (-sh - 1))) >> (-sh);
@@ -176,16 +233,28 @@ __global__ void k_split(int64_t R, int64_t K, int64_t Rpad, int64_t Kpad, const 
 }
 
 // Host side: digits and exponents of op(A) (M x K) and op(B) (rows = its N
-// columns).  Workspace (ints) holds ea[Mpad], eb[Npad], then 3 K-arrays.
-// When the two operands are the same set of vectors (op(A) = op(B)^T, a
-// symmetric rank-K update), the inner equalisation is skipped (s_k = 0).
+// columns).  Workspace (ints, slice_ints): the final row exponents ea[Mpad],
+// eb[Npad], then the raw row maxima rA[Mpad], rB[Npad] and the per-k
+// maxima kA[Kpad], kB[Kpad] (one memset clears those four).  When the two
+// operands are the same set of vectors (op(A) = op(B)^T, a symmetric
+// rank-K update), the inner equalisation is skipped (s_k = 0).
 struct SlicePlan {
   int64_t Mpad, Npad, Kpad;
   unsigned char *SA, *SB;
-  int *ea, *eb, *kA, *kB, *ksh;
+  int *ea, *eb, *rA, *rB, *kA, *kB;
 };
 
-inline size_t slice_ints(int64_t Mpad, int64_t Npad, int64_t Kpad) { return (size_t)(Mpad + Npad + 3 * Kpad); }
+inline size_t slice_ints(int64_t Mpad, int64_t Npad, int64_t Kpad) { return (size_t)(2 * (Mpad + Npad) + 2 * Kpad); }
+
+// the ints of the plan laid out from `base`
+inline void slice_layout(SlicePlan &P, int *base) {
+  P.ea = base;
+  P.eb = P.ea + P.Mpad;
+  P.rA = P.eb + P.Npad;
+  P.rB = P.rA + P.Mpad;
+  P.kA = P.rB + P.Npad;
+  P.kB = P.kA + P.Kpad;
+}
 
 inline int slice_operands(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, int64_t K,
                           const double *A, int64_t lda, const double *B, int64_t ldb, const SlicePlan &P,
@@ -193,24 +262,23 @@ inline int slice_operands(cudaStream_t st, bool transA, bool transB, int64_t M, 
   const bool a_kc = transA, b_kc = !transB;
   const bool same = (A == B) && (lda == ldb) && (transA != transB) && (M == N);
   dim3 tb(32, 8);
-  int nl = 0;
-  const int *ksh = nullptr;
-  if (!same) {
-    k_fill<<<(unsigned)ceil_div(2 * P.Kpad, 256), 256, 0, st>>>((int)(2 * P.Kpad), P.kA, EXP_NONE);
-    k_inner_exp<<<dim3((unsigned)ceil_div(M, 32), (unsigned)ceil_div(K, 32)), tb, 0, st>>>(M, K, A, lda, a_kc, P.kA);
-    k_inner_exp<<<dim3((unsigned)ceil_div(N, 32), (unsigned)ceil_div(K, 32)), tb, 0, st>>>(N, K, B, ldb, b_kc, P.kB);
-    k_kshift<<<(unsigned)ceil_div(K, 256), 256, 0, st>>>(K, P.kA, P.kB, P.ksh);
-    ksh = P.ksh;
-    nl += 4;
-  }
-  k_row_exp<<<(unsigned)ceil_div(M, 32), tb, 0, st>>>(M, K, A, lda, a_kc, ksh, +1, P.ea);
-  k_split<<<dim3((unsigned)(P.Mpad / 32), (unsigned)(P.Kpad / 32)), tb, 0, st>>>(M, K, P.Mpad, P.Kpad, A, lda, a_kc, ksh,
-                                                                                  +1, P.ea, LA, P.SA);
-  k_row_exp<<<(unsigned)ceil_div(N, 32), tb, 0, st>>>(N, K, B, ldb, b_kc, ksh, -1, P.eb);
-  k_split<<<dim3((unsigned)(P.Npad / 32), (unsigned)(P.Kpad / 32)), tb, 0, st>>>(N, K, P.Npad, P.Kpad, B, ldb, b_kc, ksh,
-                                                                                  -1, P.eb, LB, P.SB);
-  count_launch(nl + 4);
+  KernelProfiler *prof = current_profiler();
+  const size_t e0 = prof ? prof->start(st) : SIZE_MAX;
+  // per-k maxima (unless same), per-row maxima, digits: three launches
+  GS_CUDA(cudaMemsetAsync(P.rA, 0x80, (size_t)(P.Mpad + P.Npad + 2 * P.Kpad) * sizeof(int), st));
+  const int64_t Rmax = std::max(M, N);
+  if (!same)
+    k_inner_exp2<<<dim3((unsigned)ceil_div(Rmax, 32), (unsigned)ceil_div(K, 32), 2), tb, 0, st>>>(
+        M, N, K, A, lda, a_kc, B, ldb, b_kc, P.kA, P.kB);
+  const int *kA = same ? nullptr : P.kA, *kB = same ? nullptr : P.kB;
+  k_rowmax2<<<dim3((unsigned)ceil_div(Rmax, 32), (unsigned)ceil_div(K, 128), 2), tb, 0, st>>>(
+      M, N, K, A, lda, a_kc, B, ldb, b_kc, kA, kB, P.rA, P.rB);
+  k_split2<<<dim3((unsigned)(std::max(P.Mpad, P.Npad) / 32), (unsigned)(P.Kpad / 32), 2), tb, 0, st>>>(
+      M, N, K, P.Mpad, P.Npad, P.Kpad, A, lda, a_kc, B, ldb, b_kc, kA, kB, P.rA, P.rB, P.ea, P.eb, LA, LB, P.SA,
+      P.SB);
+  count_launch(same ? 2 : 3);
   GS_CHECK_LAUNCH();
+  if (prof) prof->stop(st, e0, PROF_SLICE, 0.0, 0.0);
   return GSYEIG_SUCCESS;
 }
 

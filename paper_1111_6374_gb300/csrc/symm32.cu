@@ -1,0 +1,178 @@
+// The mixed-precision operator (ke1 in FP32): Z = C W for a block W of 16
+// vectors, with C stored once per solve as fp32 tiles of its lower triangle
+// and every product accumulated in fp32.  Stored bytes are 4 n(n+1)/2, half
+// of the double-float operator's; the block of 16 reuses each stored entry
+// for 32 products.
+//
+// Layout: as the double-float operator (symv_df.cu), tile t = bi (bi + 1) /
+// 2 + bj of 64 x 64 entries, element (r, c) at (r ^ (c & 31)) + 64 c, C
+// scaled by the power of two 2^-e that brings max|C| into [1/2, 1) (exact;
+// results scaled back).  W and Z are row-major n x 16 (the 16 values of a
+// row contiguous).
+//
+// One CTA per block row i computes Z_i = sum_{j <= i} C_ij W_j +
+// sum_{j > i} C_ji^T W_j: it reads the i + 1 tiles of its row and the
+// NT - 1 - i tiles below the diagonal in its column, NT tiles for every CTA
+// (balanced), and writes its 64 rows once: no atomics, no partial sums in
+// memory, deterministic.  Each tile is read twice in all (8 n^2 bytes per
+// product); the kernel is bound by the fp32 FMA rate (32 n^2 FMAs).
+#include "mixed.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int TS = 64;
+constexpr int NB = 16;          // vectors per block
+constexpr int S32_THREADS = 256;  // thread (row r = t % 64, column quad q = t / 64)
+
+__global__ void k_f32_absmax(int64_t n, const double *__restrict__ C, int64_t ldc, unsigned long long *amax) {
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  unsigned long long mx = 0;
+  for (int idx = threadIdx.x; idx < TS * TS; idx += blockDim.x) {
+    const int r = idx % TS, c = idx / TS;
+    const int64_t i = bi * TS + r, j = bj * TS + c;
+    if (i < n && j < n) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(C[i + j * ldc]));
+      if (b < 0x7FF0000000000000ull && b > mx) mx = b;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(amax, mx);
+}
+
+__device__ __forceinline__ int scale_exp(const unsigned long long *amax) {
+  const unsigned long long b = *amax;
+  if (b == 0) return 0;
+  int e;
+  frexp(__longlong_as_double((long long)b), &e);
+  return e;
+}
+
+__global__ void k_f32_build(int64_t n, const double *__restrict__ C, int64_t ldc, const unsigned long long *amax,
+                            float *__restrict__ T) {
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  float *h = T + (bi * (bi + 1) / 2 + bj) * TS * TS;
+  const int e = scale_exp(amax);
+  for (int idx = threadIdx.x; idx < TS * TS; idx += blockDim.x) {
+    const int r = idx % TS, c = idx / TS;
+    const int64_t i = bi * TS + r, j = bj * TS + c;
+    const double v = (i < n && j < n) ? ldexp(C[i + j * ldc], -e) : 0.0;
+    h[(r ^ (c & 31)) + TS * c] = (float)v;
+  }
+}
+
+// W32 (row-major npad x 16) = V (column-major n x 16, ld ldv), zero rows past n
+__global__ void k_to_f32(int64_t n, int64_t npad, const double *__restrict__ V, int64_t ldv, float *__restrict__ W) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < npad * NB;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / NB;
+    const int c = (int)(idx % NB);
+    W[idx] = (i < n) ? (float)V[i + c * ldv] : 0.f;
+  }
+}
+
+// Z (column-major n x 16, ld ldz, FP64) = 2^e Z32
+__global__ void k_from_f32(int64_t n, const float *__restrict__ Z32, const unsigned long long *amax, double *__restrict__ Z,
+                           int64_t ldz) {
+  const int e = scale_exp(amax);
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * NB;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / NB;
+    const int c = (int)(idx % NB);
+    Z[i + c * ldz] = ldexp((double)Z32[idx], e);
+  }
+}
+
+__global__ void __launch_bounds__(S32_THREADS) k_symm32(int NT, const float *__restrict__ T, const float *__restrict__ W,
+                                                        float *__restrict__ Z) {
+  __shared__ float tile[TS * TS];
+  __shared__ float4 wj[TS][NB / 4];
+  const int i = blockIdx.x;
+  const int t = threadIdx.x, r = t % TS, q = t / TS;  // 4 column quads
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int step = 0; step < NT; step++) {
+    // steps 0..i: row tiles (i, j = step); then column tiles (j = step, i), j > i
+    const bool row = step <= i;
+    const int j = step;
+    const int bi = row ? i : j, bj = row ? j : i;
+    const float *src = T + ((int64_t)bi * (bi + 1) / 2 + bj) * TS * TS;
+    __syncthreads();  // the previous tile is no longer read
+    for (int idx = t; idx < TS * TS / 4; idx += S32_THREADS)
+      reinterpret_cast<float4 *>(tile)[idx] = reinterpret_cast<const float4 *>(src)[idx];
+    for (int idx = t; idx < TS * NB / 4; idx += S32_THREADS)
+      wj[idx / (NB / 4)][idx % (NB / 4)] = reinterpret_cast<const float4 *>(W + (int64_t)j * TS * NB)[idx];
+    __syncthreads();
+    if (row) {
+      // Z_i(r, 4q..4q+3) += sum_k C_ij(r, k) W_j(k, 4q..4q+3); a warp's lanes
+      // read 32 rows of one column: distinct banks under the swizzle
+#pragma unroll 8
+      for (int k = 0; k < TS; k++) {
+        const float c = tile[(r ^ (k & 31)) + TS * k];
+        const float4 w = wj[k][q];
+        acc.x = fmaf(c, w.x, acc.x);
+        acc.y = fmaf(c, w.y, acc.y);
+        acc.z = fmaf(c, w.z, acc.z);
+        acc.w = fmaf(c, w.w, acc.w);
+      }
+    } else {
+      // Z_i(r, .) += sum_k C_ji(k, r) W_j(k, .): column r of the stored tile
+#pragma unroll 8
+      for (int k = 0; k < TS; k++) {
+        const float c = tile[(k ^ (r & 31)) + TS * r];
+        const float4 w = wj[k][q];
+        acc.x = fmaf(c, w.x, acc.x);
+        acc.y = fmaf(c, w.y, acc.y);
+        acc.z = fmaf(c, w.z, acc.z);
+        acc.w = fmaf(c, w.w, acc.w);
+      }
+    }
+  }
+  reinterpret_cast<float4 *>(Z + ((int64_t)i * TS + r) * NB)[q] = acc;
+}
+
+}  // namespace
+
+size_t f32_operator_bytes(int64_t n) {
+  const int64_t NT = ceil_div(n, TS);
+  return (size_t)NT * (NT + 1) / 2 * TS * TS * sizeof(float) + 256;
+}
+
+size_t f32_block_bytes(int64_t n) { return (size_t)ceil_div(n, TS) * TS * NB * sizeof(float); }
+
+int f32_operator_build(cudaStream_t st, int64_t n, const double *C, int64_t ldc, F32Operator &op) {
+  const int64_t NT = ceil_div(n, TS);
+  op.n = n;
+  op.NT = NT;
+  op.npad = NT * TS;
+  op.amax = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(op.tiles) + f32_operator_bytes(n) - 256);
+  GS_CUDA(cudaMemsetAsync(op.amax, 0, sizeof(unsigned long long), st));
+  k_f32_absmax<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, C, ldc, op.amax);
+  k_f32_build<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, C, ldc, op.amax, op.tiles);
+  count_launch(2);
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int f32_symm(cudaStream_t st, const F32Operator &op, const double *V, int64_t ldv, double *Z, int64_t ldz) {
+  KernelProfiler *prof = current_profiler();
+  const size_t e0 = prof ? prof->start(st) : SIZE_MAX;
+  const unsigned g = (unsigned)std::min<int64_t>(ceil_div(op.npad * NB, 256), 4096);
+  k_to_f32<<<g, 256, 0, st>>>(op.n, op.npad, V, ldv, op.W);
+  k_symm32<<<(unsigned)op.NT, S32_THREADS, 0, st>>>((int)op.NT, op.tiles, op.W, op.Z);
+  k_from_f32<<<g, 256, 0, st>>>(op.n, op.Z, op.amax, Z, ldz);
+  count_launch(3);
+  GS_CHECK_LAUNCH();
+  if (prof) {
+    const double n = (double)op.n;
+    // algorithmic: 2 n^2 x 16 flops; the stored triangle (4 bytes per entry) once, plus W and Z
+    prof->stop(st, e0, PROF_SYMV32, 2.0 * n * n * NB, 4.0 * (n * (n + 1) / 2) + 2.0 * 4.0 * n * NB);
+  }
+  return GSYEIG_SUCCESS;
+}
+
+}  // namespace gs

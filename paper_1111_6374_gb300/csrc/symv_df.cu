@@ -18,6 +18,9 @@
 // XOR-swizzled by the column, so that a warp reading 32 rows of one column
 // and a warp reading one row of 32 columns both touch 32 distinct shared
 // memory banks); hi and lo in two arrays.
+// C is stored scaled by the power of two 2^-e that brings max|C| into
+// [1/2, 1), so that neither fp32 half overflows or underflows for pencils
+// of any scale; the row sums are scaled back by 2^e.
 // Diagonal tiles hold the full symmetric 64 x 64 block.  Partials go to
 // W[slot][row]: tile (bi, bj) writes its row sums to slot bj of rows in
 // block bi and (off-diagonal) its column sums to slot bi of rows in block
@@ -50,21 +53,56 @@ __device__ __forceinline__ void acc2(float &s, float &c, float p, float e) {
   c += q + e;
 }
 
-// Tiles of the lower triangle of M: M = C (trans = 0) or M = C^T (trans =
-// 1, read from C's upper triangle); with tri = 1 the entries above the
+// Largest |entry| of the stored part of M (as its bit pattern: for
+// non-negative doubles the integer order is the numeric order) into *amax.
+__global__ void k_op_absmax(int64_t n, const double *__restrict__ C, int64_t ldc, int tri, int trans,
+                            unsigned long long *amax) {
+  const int64_t bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  unsigned long long mx = 0;
+  for (int idx = threadIdx.x; idx < TS * TS; idx += blockDim.x) {
+    const int r = idx % TS, c = idx / TS;
+    const int64_t i = bi * TS + r, j = bj * TS + c;
+    if (i < n && j < n && !(tri && j > i)) {
+      const double v = trans ? C[j + i * ldc] : C[i + j * ldc];
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+      if (b < 0x7FF0000000000000ull && b > mx) mx = b;  // finite entries only
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(amax, mx);
+}
+
+// the power of two 2^e with max|M| 2^-e in [1/2, 1) (e = 0 for M = 0)
+__device__ __forceinline__ int op_exponent(const unsigned long long *amax) {
+  const unsigned long long b = *amax;
+  if (b == 0) return 0;
+  int e;
+  frexp(__longlong_as_double((long long)b), &e);
+  return e;
+}
+
+// Tiles of the lower triangle of M 2^-e: M = C (trans = 0) or M = C^T (trans
+// = 1, read from C's upper triangle); with tri = 1 the entries above the
 // diagonal of the diagonal tiles are stored as zeros (M lower triangular),
-// else the diagonal tiles hold the full symmetric block.
+// else the diagonal tiles hold the full symmetric block.  The exact scaling
+// by 2^-e (e from op_exponent) keeps the fp32 hi/lo pair inside fp32's range
+// whatever the magnitude of M; the products are scaled back by 2^e.
 __global__ void k_op_build(int64_t n, int64_t NT, const double *__restrict__ C, int64_t ldc, int tri, int trans,
-                           float *__restrict__ hi, float *__restrict__ lo) {
+                           const unsigned long long *amax, float *__restrict__ hi, float *__restrict__ lo) {
   const int64_t bi = blockIdx.y, bj = blockIdx.x;
   if (bj > bi) return;
   const int64_t t = bi * (bi + 1) / 2 + bj;
   float *h = hi + t * TS * TS, *l = lo + t * TS * TS;
+  const int e = op_exponent(amax);
   for (int idx = threadIdx.x; idx < TS * TS; idx += blockDim.x) {
     const int r = idx % TS, c = idx / TS;
     const int64_t i = bi * TS + r, j = bj * TS + c;
     double v = 0.0;
-    if (i < n && j < n && !(tri && j > i)) v = trans ? C[j + i * ldc] : C[i + j * ldc];
+    if (i < n && j < n && !(tri && j > i)) v = ldexp(trans ? C[j + i * ldc] : C[i + j * ldc], -e);
     const float vh = (float)v;
     const int pos = (r ^ (c & 31)) + TS * c;
     h[pos] = vh;
@@ -104,6 +142,17 @@ constexpr uint32_t SPIN_LIMIT = 1u << 24;
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
   for (uint32_t it = 0; it < limit; it++) {
     uint32_t done;
+    if (limit < SPIN_LIMIT) {
+      // a test limit: poll without the hardware's suspended wait, so that
+      // the limit counts polls and the wait can run out
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(sptr(bar)), "r"(parity)
+          : "memory");
+      if (done) return true;
+      continue;
+    }
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -255,7 +304,8 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
 // DF_SYM; the tiles' column blocks 0..b for DF_ROWS and b..NT-1 for DF_COLS,
 // b = i / 64), accumulated in double-float and rounded to FP64 once.
 __global__ void k_reduce_slots(int64_t n, int64_t npad, int64_t NT, const float2 *__restrict__ W, double *__restrict__ z,
-                               int mode) {
+                               int mode, const unsigned long long *amax) {
+  const int e = op_exponent(amax);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
     const int64_t blk = i / TS;
@@ -267,16 +317,18 @@ __global__ void k_reduce_slots(int64_t n, int64_t npad, int64_t NT, const float2
     }
     if (q < q1) a = df_add(a, W[q * npad + i]);
     a = df_add(a, b);
-    z[i] = (double)a.x + (double)a.y;
+    z[i] = ldexp((double)a.x + (double)a.y, e);
   }
 }
 
 }  // namespace
 
-size_t df_operator_bytes(int64_t n) {
+size_t df_tile_bytes(int64_t n) {
   const int64_t NT = ceil_div(n, TS);
   return (size_t)NT * (NT + 1) / 2 * TS * TS * sizeof(float) * 2;
 }
+
+size_t df_operator_bytes(int64_t n) { return df_tile_bytes(n) + 256; }
 
 size_t df_partials_bytes(int64_t n) {
   const int64_t NT = ceil_div(n, TS);
@@ -290,8 +342,12 @@ int df_operator_build(cudaStream_t st, int64_t n, const double *C, int64_t ldc, 
   op.npad = NT * TS;
   const size_t tiles = (size_t)NT * (NT + 1) / 2 * TS * TS;
   op.lo = op.hi + tiles;
-  k_op_build<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, NT, C, ldc, tri ? 1 : 0, trans ? 1 : 0, op.hi, op.lo);
-  count_launch();
+  op.amax = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(op.hi) + df_tile_bytes(n));
+  GS_CUDA(cudaMemsetAsync(op.amax, 0, sizeof(unsigned long long), st));
+  k_op_absmax<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, C, ldc, tri ? 1 : 0, trans ? 1 : 0, op.amax);
+  k_op_build<<<dim3((unsigned)NT, (unsigned)NT), 256, 0, st>>>(n, NT, C, ldc, tri ? 1 : 0, trans ? 1 : 0, op.amax,
+                                                               op.hi, op.lo);
+  count_launch(2);
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
 }
@@ -319,11 +375,11 @@ int df_symv(cudaStream_t st, const DfOperator &op, const double *w, double *z, i
   k_vec_split<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.npad, 256), 1024)), 256, 0, st>>>(
       op.n, op.npad, w, op.wsplit);
   const size_t smem = (size_t)NSTAGE * 2 * TILE_BYTES + NSTAGE * sizeof(uint64_t);
-  GS_CUDA(cudaFuncSetAttribute((const void *)k_symv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GS_TRY(set_max_smem((const void *)k_symv_df, (int)smem));
   k_symv_df<<<(unsigned)std::min<int64_t>(ntiles, (int64_t)num_sms_cached() * CTAS_PER_SM), DF_THREADS, smem, st>>>(
       (int)op.NT, op.npad, op.hi, op.lo, op.wsplit, op.W, op.err, mode, op.spin > 0 ? op.spin : SPIN_LIMIT);
   k_reduce_slots<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(op.n, 256), 1024)), 256, 0, st>>>(
-      op.n, op.npad, op.NT, op.W, z, mode);
+      op.n, op.npad, op.NT, op.W, z, mode, op.amax);
   count_launch(3);
   GS_CHECK_LAUNCH();
   if (prof) {

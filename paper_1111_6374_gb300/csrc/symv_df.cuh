@@ -13,13 +13,14 @@ struct DfOperator {
   float2 *wsplit = nullptr;            // npad split input vector
   int *err = nullptr;                  // device flag: a bounded wait of the symv kernel expired
   uint32_t spin = 0;                   // poll limit of the kernel's main-loop waits (0 = the default bound)
+  unsigned long long *amax = nullptr;  // device: max |entry| (bits) of the stored matrix, after the tiles
 };
 
 // Products with the stored lower triangle: the symmetric matrix it
 // completes, or the lower-triangular matrix L itself, or L^T.
 enum DfMode { DF_SYM = 0, DF_ROWS = 1, DF_COLS = 2 };
 
-size_t df_operator_bytes(int64_t n);
+size_t df_operator_bytes(int64_t n);  // the tiles plus the operator's scale
 size_t df_partials_bytes(int64_t n);  // W, wsplit and the error flag together
 // Fill op.hi/op.lo from the lower triangle of C (trans = false) or of C^T
 // (trans = true, i.e. C's upper triangle); tri = true stores a lower-

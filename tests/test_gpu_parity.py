@@ -518,3 +518,25 @@ def test_solve_implicit_variant_ki_matches_oracle(n, s, inverse):
     G = _np(dB if inverse else dA)
     G0 = B if inverse else A
     assert np.array_equal(G, G0), "KI must leave the untransformed matrix as it was"
+
+
+@pytest.mark.parametrize("n,s,inverse", [(1024, 16, 1), (2048, 32, 1), (1000, 12, 1), (768, 8, 0)])
+def test_solve_mixed_precision_matches_oracle(n, s, inverse):
+    """opts.mixed: block Lanczos (block 16) on the fp32 operator with fp32
+    accumulation, FP64 reorthogonalisation, then the FP64 block refinement
+    on C; the oracle's pairs at the same 1e-10 gates as the FP64 path."""
+    from paper_1111_6374_gb300 import Solver
+
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=n + s + 5))
+    w_or, X_or = oracle.gsyeig(A, B, s)
+    w, X, info = Solver(0, mixed=1, inverse=inverse).solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s)
+    assert info["inverse"] == inverse and info["nconv"] >= s
+    assert info["block_steps"] > 0 and info["refine_iters"] >= 0
+    w, X = _np(w), _np(X)
+    cn = np.abs(lam).max()
+    assert np.all(np.abs(w - w_or) <= 1e-10 * np.abs(w_or) + (0 if inverse else 1e-14 * cn))
+    et = _checks.eta(A, B, w, X)
+    assert et.max() <= 1e-10
+    assert _checks.b_orth_err(B, X) <= 1e-10
+    ang, lim = _checks.max_subspace_angle(B, X, X_or, w, lam, cn, 1e-12 * cn)
+    assert ang <= lim, (ang, lim)

@@ -269,3 +269,92 @@ def test_subspace_angle_helper_detects_rotation():
     Y[:, 1] = np.cos(t) * X[:, 1] + np.sin(t) * np.eye(n)[:, 10]
     ang, _ = _checks.max_subspace_angle(B, Y, X, w, lam, 40.0, 1e-12)
     assert abs(ang - np.sin(t)) < 1e-12
+
+
+# ---- the warm-start network's oracle (oracle/mlp.py) -----------------------
+
+def test_mlp_oracle_bf16_rounding_known_values():
+    """bf16 keeps 8 significant bits: ties go to the even neighbour."""
+    from oracle import mlp
+
+    x = np.array([1.0, 1 + 2.0**-8, 1 + 3 * 2.0**-8, 1 + 2.0**-8 + 2.0**-20, -2.5, 3.14159, 0.0, 2.0**-130])
+    want = np.array([1.0, 1.0, 1 + 2.0**-6, 1 + 2.0**-7, -2.5, 3.140625, 0.0, 2.0**-130])
+    assert np.array_equal(mlp.bf16_round(x), want)
+
+
+def test_mlp_oracle_identity_network():
+    """n_in = H = n_out, W = I, b = 0 and X >= 0: both ReLUs pass X through, Y = X."""
+    from oracle import mlp
+
+    n = 16
+    I = np.eye(n).ravel()
+    p = np.concatenate([I, np.zeros(n), I, np.zeros(n), I, np.zeros(n)])
+    X = np.random.default_rng(1).uniform(0, 1, (5, n))
+    Y, _, _ = mlp.forward(p, X, n, n, n, bf16=False)
+    assert np.array_equal(Y, X)
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    """Back-propagation of the FP64 network against central differences of
+    the loss in every parameter (a dropped term, a wrong transpose or a
+    wrong ReLU mask fails this)."""
+    from oracle import mlp
+
+    r = np.random.default_rng(2)
+    n_in, H, n_out, batch = 5, 16, 3, 7
+    P = H * n_in + H + H * H + H + n_out * H + n_out
+    p = r.standard_normal(P) * 0.5
+    X = r.standard_normal((batch, n_in))
+    T = r.standard_normal((batch, n_out))
+    wo = np.array([2.0, 0.5, 1.0])
+    _, g = mlp.loss_and_grad(p, X, T, n_in, H, n_out, wo, bf16=False)
+    h = 1e-6
+    num = np.empty(P)
+    for i in range(P):
+        e = np.zeros(P)
+        e[i] = h
+        lp, _ = mlp.loss_and_grad(p + e, X, T, n_in, H, n_out, wo, bf16=False)
+        lm, _ = mlp.loss_and_grad(p - e, X, T, n_in, H, n_out, wo, bf16=False)
+        num[i] = (lp - lm) / (2 * h)
+    assert np.abs(num - g).max() <= 1e-6 * max(1.0, np.abs(g).max())
+
+
+def test_mlp_oracle_adam_first_step_closed_form():
+    """From zero moments the bias-corrected first step is lr g / (|g| + eps)."""
+    from oracle import mlp
+
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p1, m, v = mlp.adam(np.zeros(4), np.zeros(4), np.zeros(4), g, 1, 0.01)
+    assert np.allclose(p1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+def test_pencil_sequence_spectrum_is_lambda_of_t():
+    """The sequence generator's low-rank update reproduces A(t) = U^T Q(t)
+    diag(lam(t)) Q(t)^T U: the generalized eigenvalues of (A(t), B) are
+    lam0 + t d (scipy's generalized symmetric eigensolver as the check)."""
+    import scipy.linalg
+
+    import inputs
+
+    seq = inputs.PencilSequence(96, seed=4, dt=0.05)
+    for k in (0, 3, 17):
+        A, B, lam = seq.pencil(k)
+        w = scipy.linalg.eigh(A.numpy(), B.numpy(), eigvals_only=True)
+        assert np.abs(w - lam.numpy()).max() <= 1e-9 * 1000
+
+
+def test_structured_pencil_spectrum_is_lambda():
+    """The O(n^2) stand-in pencil (reflector Q, banded U): its generalized
+    eigenvalues are the drawn lambda (scipy's generalized eigensolver)."""
+    import scipy.linalg
+
+    import inputs
+
+    import torch
+
+    A, B, lam = inputs.make_pencil_structured(160, seed=3, reflectors=5, band=3)
+    assert torch.equal(A, A.T) and torch.equal(B, B.T)
+    w = scipy.linalg.eigh(A.numpy(), B.numpy(), eigvals_only=True)
+    assert np.abs(w - lam.numpy()).max() <= 1e-9 * 1000
+    assert np.linalg.eigvalsh(B.numpy()).min() > 0.5
