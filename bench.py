@@ -253,7 +253,7 @@ def run_ours(args, ws, rank, local):
         A0, B0, lam = inputs.make_pencil(n, seed=args.seed + rank, device=dev)
     A = torch.empty_like(A0)
     B = torch.empty_like(B0)
-    solver = Solver(local, inverse=1 if args.route == "inverse" else 0, block=args.block)
+    solver = Solver(local, inverse=1 if args.route == "inverse" else 0, block=args.block, graph=args.graph)
     stream = torch.cuda.current_stream(dev)
 
     def restore():
@@ -422,7 +422,7 @@ def run_ours(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "s": s, "which": "smallest", "route": ROUTES[args.route],
-                   "inverse_used": last["inverse"], "krylov_dim": last["krylov_dim"],
+                   "inverse_used": last["inverse"], "krylov_dim": last["krylov_dim"], "graph": args.graph,
                    "keep": last["keep"], "tol": 1e-12, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (2 x %.1f GB vs 129 MB)" % (n * n * 8 / 1e9)},
         "stages_ms": {k: last[k] for k in ("ms_gs1", "ms_gs2", "ms_ke", "ms_ke3", "ms_bt1", "ms_total")},
@@ -456,6 +456,231 @@ def run_ours(args, ws, rank, local):
     # a time that does not meet the accuracy the metric is quoted at is not a result
     return 0 if acc_ok else 3
 
+
+
+# ---- the three extensions of the route, each against the plain path ----------
+#
+# `--next mixed|batched|warm` runs one of them instead of the headline and
+# prints one JSON line with its own metric; the timed region of each is
+# stated in the line.
+
+
+def _accuracy(A, B, w, X, lam, lam_max):
+    """Relative eigenvalue error against the constructed spectrum, backward
+    error eta and B-orthonormality (device tensors).  The eigenvalue gate
+    is |d lambda| <= 1e-10 |lambda| + 1e-14 max|lambda|: the pencil itself is
+    formed in FP64, so an eigenvalue near zero is known only to about
+    eps ||A|| (the floor of any backward-stable solve)."""
+    import torch
+
+    d = (w - lam).abs()
+    rel = float((d / lam.abs()).max())
+    gate = float((d / (1e-10 * lam.abs() + 1e-14 * lam_max)).max())
+    R = A @ X - (B @ X) * w
+    eta = float((R.norm(dim=0) / ((_power(A) + w.abs() * _power(B)) * X.norm(dim=0))).max())
+    orth = float((X.T @ (B @ X) - torch.eye(X.shape[1], device=X.device, dtype=X.dtype)).abs().max())
+    return {"max_rel_eig_err_vs_constructed": rel, "eig_gate_ratio": gate, "max_eta": eta, "orth_err": orth,
+            "ok": bool(gate <= 1.0 and eta <= 1e-10 and orth <= 1e-10)}
+
+
+def _event_time(fn, stream):
+    import torch
+
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def next_mixed(args, dev):
+    """Mixed precision against plain FP64 on one structured pencil (order
+    args.n, default 65536, s = 256 smallest, inverse route): warm-up solves,
+    then one timed solve each, inputs restored between solves outside the
+    timed interval.  The operator's inputs (2 x 34 GB at n = 65536) are far
+    larger than L2."""
+    import torch
+
+    import inputs
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = args.n, args.s
+    t0 = time.perf_counter()
+    A0, B0, lam = inputs.make_pencil_structured(n, seed=args.seed, device=dev)
+    gen_s = time.perf_counter() - t0
+    A, B = torch.empty_like(A0), torch.empty_like(B0)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, opts in (("mixed", dict(mixed=1)), ("mixed_block_refinement", dict(mixed=2)),
+                       ("plain_fp64_route", dict(mixed=0))):
+        sol = Solver(dev.index, inverse=1, **opts)
+        for _ in range(args.warmup):
+            A.copy_(A0)
+            B.copy_(B0)
+            sol.solve(A, B, s, overwrite=True)
+        ts, info = [], None
+        for _ in range(args.steps):
+            A.copy_(A0)
+            B.copy_(B0)
+            ms, (w, X, info) = _event_time(lambda: sol.solve(A, B, s, overwrite=True), stream)
+            ts.append(ms)
+        acc = _accuracy(A0, B0, w, X, lam[:s], float(lam.abs().max()))
+        out[name] = {"ms_per_step": statistics.mean(ts), "steps": len(ts), "accuracy": acc,
+                     "stages_ms": {k: info[k] for k in ("ms_gs1", "ms_gs2", "ms_ke", "ms_ke3", "ms_bt1", "ms_total")},
+                     "matvecs": info["matvecs"], "restarts": info["restarts"]}
+        if name.startswith("mixed"):
+            out[name].update({k: info[k] for k in ("block_steps", "refine_iters", "ms_block_lanczos", "ms_refine",
+                                                    "refine_fallback", "breakdowns")})
+        if name == "mixed":
+            # one more solve with CUDA events around every kernel class
+            A.copy_(A0)
+            B.copy_(B0)
+            sol.set_options(profile=1)
+            _, _, pi = sol.solve(A, B, s, overwrite=True)
+            sol.set_options(profile=0)
+            out[name]["profiled_classes_ms"] = {
+                "symm32 (fp32 block operator)": pi["symm32_ms"], "symv (double-float operator)": pi["symv_ms"],
+                "orth (FP64 CGS2 of both stages)": pi["orth_ms"], "gemm engine": pi["gemm_ms"],
+                "ritz": pi["ritz_ms"], "restart": pi["restart_ms"], "symm32_launches": pi["symm32_launches"]}
+        if name == "mixed":
+            w_mixed = w
+        else:
+            out[name]["eig_diff_vs_mixed"] = float(((w - w_mixed).abs() / w.abs()).max())
+        del w, X
+        sol.close()
+        torch.cuda.empty_cache()
+    m, p = out["mixed"], out["plain_fp64_route"]
+    return {"leg": "mixed", "metric": METRIC, "value": m["ms_per_step"] / 1e3, "unit": "s",
+            "higher_is_better": False, "dtype": "f32 operator, f64 elsewhere", "data": "synthetic",
+            "config": {"workload": f"gsyeig n={n} s={s} smallest, structured known-spectrum pencil "
+                                   f"(16 reflectors, banded U), mixed precision vs plain FP64 route",
+                       "n": n, "s": s, "route": ROUTES["inverse"], "generate_s": gen_s,
+                       "l2": "inputs larger than L2"},
+            "speedup_vs_plain": p["ms_per_step"] / m["ms_per_step"], "mixed": m, "plain": p,
+            "mixed_block_refinement": out["mixed_block_refinement"],
+            "accuracy_ok": all(out[k]["accuracy"]["ok"] for k in out)}
+
+
+def next_batched(args, dev):
+    """64 independent problems, n uniform over the multiples of 64 in
+    [512, 4096], s = 16 smallest, seeds 1000 + i: one gsyeig_solve_batched
+    call (graph-captured Lanczos cycles, autotuned panel width, 8 streams)
+    against the same 64 problems solved one after another by the plain
+    solver, both on the inverse route.  Each timed region covers all 64 solves; inputs are restored
+    outside it."""
+    import numpy as np
+    import torch
+
+    import inputs
+    from paper_1111_6374_gb300 import Solver
+
+    count, s = args.batch, 16
+    rng = np.random.default_rng(args.seed)
+    ns = [int(x) for x in rng.choice(np.arange(512, 4097, 64), count)]
+    pristine = [inputs.make_pencil(n, seed=1000 + i, device=dev) for i, n in enumerate(ns)]
+    work = [(torch.empty_like(A), torch.empty_like(B)) for A, B, _ in pristine]
+    stream = torch.cuda.current_stream(dev)
+
+    def restore():
+        for (A0, B0, _), (A, B) in zip(pristine, work):
+            A.copy_(A0)
+            B.copy_(B0)
+
+    # the inverse route for both (every pencil here has A positive definite):
+    # its smallest lambda = 1/mu are resolved to 1e-10 relative
+    bsol = Solver(dev.index, graph=1, inverse=1)
+    psol = Solver(dev.index, inverse=1)
+    t0 = time.perf_counter()
+    tuned = {n: bsol.autotuned_block(n) for n in sorted(set(ns))}
+    tune_s = time.perf_counter() - t0
+    bt, pt = [], []
+    for it in range(args.warmup + args.steps):
+        restore()
+        ms, res = _event_time(lambda: bsol.solve_batched(work, s, streams=8, overwrite=True), stream)
+        if it >= args.warmup:
+            bt.append(ms)
+    acc = [_accuracy(A0, B0, w, X, lam[:s], float(lam.abs().max())) for (A0, B0, lam), (w, X, _) in zip(pristine, res)]
+    wb = [w.clone() for w, _, _ in res]
+    del res
+    for it in range(args.warmup + args.steps):
+        restore()
+        ms, res = _event_time(lambda: [psol.solve(A, B, s, overwrite=True) for A, B in work], stream)
+        if it >= args.warmup:
+            pt.append(ms)
+    diff = max(float(((w - r[0]).abs() / r[0].abs()).max()) for w, r in zip(wb, res))
+    mb, mp = statistics.mean(bt), statistics.mean(pt)
+    return {"leg": "batched", "metric": "time-to-solution of the whole batch", "value": mb / 1e3, "unit": "s",
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{count} problems, n uniform on multiples of 64 in [512, 4096], s={s} smallest, "
+                                   "known-spectrum pencils, seeds 1000+i", "orders": ns,
+                       "streams": 8, "graph": True, "panel_width_by_n": tuned, "autotune_s": tune_s},
+            "steps": len(bt), "warmup": args.warmup, "ms_batched": mb, "ms_sequential": mp, "speedup": mp / mb,
+            "max_rel_diff_batched_vs_sequential": diff,
+            "accuracy": {"max_rel_eig_err": max(a["max_rel_eig_err_vs_constructed"] for a in acc),
+                         "max_eig_gate_ratio": max(a["eig_gate_ratio"] for a in acc),
+                         "max_eta": max(a["max_eta"] for a in acc), "max_orth_err": max(a["orth_err"] for a in acc)},
+            "accuracy_ok": all(a["ok"] for a in acc)}
+
+
+def next_warm(args, dev):
+    """The learned warm start over a sequence of related pencils (n =
+    args.n, default 8192, s = 64, 200 problems, dt = 0.005): the first 150
+    solved from random starts give the training data; the network (two
+    hidden layers of 256) trains on the GPU; the last 50 are solved from a
+    random start, from the previous eigenvectors, and from the learned
+    extrapolation.  Times are CUDA-event times of each solve (the pencil of
+    each step is built outside them)."""
+    import torch
+
+    import inputs
+    from paper_1111_6374_gb300 import warmstart
+
+    n, s, T, T_train = args.n, args.s, args.seq_len, args.seq_train
+    seq = inputs.PencilSequence(n, seed=args.seed, device=dev)
+    worst = {"rel": 0.0, "gate": 0.0, "eta": 0.0, "orth": 0.0, "ok": True}
+
+    def check(A, B, w, X, lam):
+        a = _accuracy(A, B, w, X, lam[:s], float(lam.abs().max()))
+        worst["rel"] = max(worst["rel"], a["max_rel_eig_err_vs_constructed"])
+        worst["gate"] = max(worst["gate"], a["eig_gate_ratio"])
+        worst["eta"] = max(worst["eta"], a["max_eta"])
+        worst["orth"] = max(worst["orth"], a["orth_err"])
+        worst["ok"] &= a["ok"]
+
+    stats, hist, train_ms = warmstart.evaluate_sequence(seq.pencil, seq.B, n, s, T, T_train, iters=args.train_iters,
+                                                        check=check, device=dev.index)
+    per = {m: {"matvecs": v[0], "ms": v[1], "restarts": v[2], "ms_per_solve": v[1] / (T - T_train),
+               "matvecs_per_solve": v[0] / (T - T_train)} for m, v in stats.items()}
+    return {"leg": "warm", "metric": "solve time over the sequence's last problems", "value": per["learned"]["ms"] / 1e3,
+            "unit": "s", "higher_is_better": False, "dtype": "f64 solve, bf16 network", "data": "synthetic",
+            "config": {"workload": f"sequence of {T} related pencils n={n} s={s} (8 moving reflectors, "
+                                   f"lambda(t) = lambda0 + t d, dt = 0.005), trained on the first {T_train}",
+                       "n": n, "s": s, "T": T, "T_train": T_train, "train_iters": args.train_iters},
+            "methods": per, "train_ms": train_ms, "loss_first_last": [hist[0], hist[-1]],
+            "speedup_vs_random": per["random"]["ms"] / per["learned"]["ms"],
+            "speedup_vs_reuse": per["reuse"]["ms"] / per["learned"]["ms"],
+            "accuracy": {"max_rel_eig_err": worst["rel"], "max_eig_gate_ratio": worst["gate"], "max_eta": worst["eta"],
+                         "max_orth_err": worst["orth"]},
+            "accuracy_ok": worst["ok"]}
+
+
+def run_next(args, ws, rank, local):
+    import torch
+
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "bench.py needs a CUDA GPU"}), flush=True)
+        return 2
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    leg = {"mixed": next_mixed, "batched": next_batched, "warm": next_warm}[args.next]
+    with ClockSampler(local) as clk:
+        line = leg(args, dev)
+    line["clocks"] = clk.summary()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0 if line.get("accuracy_ok") else 3
 
 def _library_point(A0, B0, s, lam):
     """cuSOLVER (torch.linalg) on the same pencil and GPU, for comparison
@@ -513,8 +738,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=16384)
-    ap.add_argument("--s", type=int, default=100)
+    ap.add_argument("--n", type=int, default=None, help="order (default 16384; --next: 65536 mixed, 8192 warm)")
+    ap.add_argument("--s", type=int, default=None, help="wanted pairs (default 100; --next: 256 mixed, 64 warm)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-sample-n", type=int, default=4096)
@@ -527,13 +752,27 @@ def main(argv=None):
     ap.add_argument("--gen-device", choices=["cuda", "cpu"], default="cuda",
                     help="where the synthetic pencil is built (input generation only, outside any timing)")
     ap.add_argument("--block", type=int, default=0, help="panel width nb of the blocked factorisations (0 = default)")
+    ap.add_argument("--graph", type=int, choices=[0, 1], default=0,
+                    help="1: replay the Lanczos cycles from CUDA graphs (gsyeig_opts.graph)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the comparison solves (variant KI, plain FP64, cuSOLVER)")
+    ap.add_argument("--next", choices=["mixed", "batched", "warm"], default=None,
+                    help="run one extension of the route (mixed precision, a batch, the learned warm start) "
+                         "against the plain path instead of the headline")
+    ap.add_argument("--batch", type=int, default=64, help="--next batched: number of problems")
+    ap.add_argument("--seq-len", type=int, default=200, help="--next warm: problems in the sequence")
+    ap.add_argument("--seq-train", type=int, default=150, help="--next warm: problems used for training")
+    ap.add_argument("--train-iters", type=int, default=2000, help="--next warm: Adam iterations")
     args = ap.parse_args(argv)
+    n_def, s_def = {None: (16384, 100), "mixed": (65536, 256), "batched": (0, 16), "warm": (8192, 64)}[args.next]
+    args.n = n_def if args.n is None else args.n
+    args.s = s_def if args.s is None else args.s
     args.workload = f"gsyeig n={args.n} s={args.s} smallest, FP64, known-spectrum synthetic pencil"
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.next:
+        return run_next(args, ws, rank, local)
     return run_ours(args, ws, rank, local)
 
 

@@ -127,13 +127,19 @@ typedef struct {
    * check_every Lanczos steps (once the projected matrix holds the kept pairs), so that a good
    * start can stop before the Krylov dimension is reached; 0 (default): at the end of a cycle only. */
   int32_t check_every;
-  /* 1: mixed precision for the Lanczos stage (the paper's operator is the per-iteration cost, Section
-   * 2.3): block Lanczos (block size 16) with C streamed as fp32 tiles and fp32 accumulation, FP64
-   * reorthogonalisation (CGS2) and projected matrix, then an FP64 block refinement (LOBPCG on the
-   * k = s + max(16, s/8) Ritz vectors, Rayleigh-Ritz on [X, R, P] with the products by C on the
-   * FP64-accurate tensor-core engine) until the s wanted residuals meet tol ||C||.  krylov_dim is the
-   * block Krylov dimension (default min(max(5s, s + 64)) rounded up to 16).  gs1, gs2 and bt1 are
-   * unchanged.  On the inverse route B's definiteness is not checked.  Not with implicit = 1. */
+  /* Mixed precision for the Lanczos stage (the paper's operator is the per-iteration cost, Section
+   * 2.3).  Both forms start with block Lanczos (block size 16) with C streamed as fp32 tiles and
+   * fp32 accumulation, FP64 reorthogonalisation (CGS2) and projected matrix, giving the k = s +
+   * max(16, s/8) Ritz vectors of the band matrix (krylov_dim is the block Krylov dimension, default
+   * max(3s, s + 64) for mixed = 1 and max(5s, s + 64) for mixed = 2, rounded up to 16).  Then:
+   * 1: the FP64-accurate Lanczos (ke1 on the double-float operator) started from the sum of the s
+   *    wanted fp32 Ritz vectors, with Ritz tests every check_every steps (16 if 0), so that it stops
+   *    once the s pairs meet the tolerance;
+   * 2: an FP64 block refinement (LOBPCG on the k vectors, Rayleigh-Ritz on an orthonormal [X, P, W]
+   *    with the products by C on the FP64-accurate tensor-core engine) until the s wanted residuals
+   *    meet tol ||C||; if it cannot, the FP64 Lanczos stage runs from a random start (info
+   *    refine_fallback).
+   * gs1, gs2 and bt1 are unchanged.  Not with implicit = 1. */
   int32_t mixed;
   /* 1: each Lanczos cycle (without check_every) is captured once into a CUDA graph and replayed
    * while the handle's buffers and the operator stay the same: one host launch per cycle instead of
@@ -142,6 +148,11 @@ typedef struct {
   /* > 0: at most this many CTAs (SMs) for the persistent tensor-core GEMM, so that the problems of a
    * batch solved concurrently on several streams share the GPU; 0 = one CTA per SM. */
   int32_t max_ctas;
+  /* 1, with start_block (start_cols >= s columns): start from the whole block instead of one vector:
+   * the FP64 block refinement of the mixed route (LOBPCG, products on the tensor-core engine) runs
+   * directly from the block F X0 plus max(8, s/4) random guard columns, with no Lanczos stage; for a
+   * sequence of related problems whose eigenvectors move little from one problem to the next. */
+  int32_t block_start;
 } gsyeig_opts;
 
 /* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
@@ -183,9 +194,16 @@ typedef struct {
                              from the Krylov space: a filter_edge for a following solve) */
   int64_t filter_matvecs; /* operator applications of the start vector's Chebyshev filter */
   double slice_ms;        /* opts.profile = 1: event time of the kernels slicing GEMM operands into digits */
-  /* opts.mixed = 1: fp32 block steps, FP64 refinement iterations and the event time of both stages */
+  /* opts.mixed: fp32 block steps, FP64 block-refinement iterations (mixed = 2) and the event time of
+   * the fp32 stage and of the FP64 stage that follows it */
   int64_t block_steps, refine_iters;
   double ms_block_lanczos, ms_refine;
+  int64_t refine_stop;     /* 1: the block refinement stopped on numerically dependent residuals; 2: its
+                              observed rate did not reach the tolerance within 60 steps */
+  int64_t refine_fallback; /* 1: the block refinement did not converge and the FP64 Lanczos stage ran */
+  /* opts.profile = 1: launches and event time of the fp32 block operator of the mixed stage */
+  int64_t symm32_launches;
+  double symm32_ms;
 } gsyeig_info;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t
@@ -331,17 +349,24 @@ int gsyeig_mlp_adam(float *params, float *m, float *v, const float *grad, int64_
  * scal[0..1] (device doubles) = theta[s-1], g for decoding. */
 int gsyeig_ws_features(int64_t s, const double *theta, const double *theta_prev, double dt_rel, float *features,
                        double *scal, void *stream);
-/* Training targets of those features from the successor's solution:
- * t[0] = (theta_next[s-1] - scal[0]) / scal[1], t[1+j] = || P[:, j] || with P
- * = X_next^T B X (s x s, ld ldp) the overlaps of the previous eigenvectors
- * with the successor's, capped at 1 (s + 1 targets). */
-int gsyeig_ws_targets(int64_t s, const double *theta_next, const double *scal, const double *P, int64_t ldp,
-                      float *targets, void *stream);
-/* Network outputs (s + 1) to a warm start: weights[j] = clamp(o[1+j], wmin,
- * 1) for opts.start_weights and *cut = scal[0] + scal[1] (o[0] + margin) for
- * opts.filter_cut (device doubles). */
-int gsyeig_ws_decode(int64_t s, const float *outputs, const double *scal, double margin, double wmin, double *weights,
-                     double *cut, void *stream);
+/* Block warm start (opts.block_start): the network proposes, for each
+ * eigenvector of the last solved problem, how far to extrapolate it along
+ * the sequence.  gsyeig_ws_align: out_j = sgn_j Y[:, pi_j] - X[:, j], where
+ * pi_j is the column of Y with the largest |P[j, i]| (P = X^T B Y, s x s, ld
+ * ldp) and sgn_j that overlap's sign; columns whose best |overlap| is below
+ * 1/2 (eigenvalue crossings) get 0; match (s floats, may be NULL) gets the
+ * best |overlap| of every column.  gsyeig_ws_coef_targets: the B-optimal
+ * extrapolation coefficients t_j = clamp(-(D_j^T BE_j) / (D_j^T BD_j), lo,
+ * hi) of training data (D = align(X(t), X(t-1)), E = align(X(t), X(t+1)),
+ * BD = B D, BE = B E).  gsyeig_ws_extrapolate: out_j = X_j - clamp(c_j, lo,
+ * hi) D_j, the start block proposed for the next problem.  All device
+ * pointers, column-major, enqueued on `stream`. */
+int gsyeig_ws_align(int64_t n, int64_t s, const double *X, int64_t ldx, const double *Y, int64_t ldy, const double *P,
+                    int64_t ldp, double *out, int64_t ldo, float *match, void *stream);
+int gsyeig_ws_coef_targets(int64_t n, int64_t s, const double *D, int64_t ldd, const double *BD, int64_t ldbd,
+                           const double *BE, int64_t ldbe, double lo, double hi, float *targets, void *stream);
+int gsyeig_ws_extrapolate(int64_t n, int64_t s, const double *X, int64_t ldx, const double *D, int64_t ldd,
+                          const float *coef, double lo, double hi, double *out, int64_t ldo, void *stream);
 
 /* ---- batches of independent problems ---------------------------------- */
 /* One problem of a batch: the arguments of gsyeig_solve (device pointers). */

@@ -217,6 +217,11 @@ int64_t oracle_sturm_count(int64_t n, const double *d, const double *e, double x
 /* applied as a chain of Givens rotations from the bottom of the block up.  */
 /* e is destroyed.  Eigenvalues are returned sorted ascending (vectors      */
 /* permuted alike).  Returns 0, or -1 if some block needed > 60 sweeps.     */
+/* The method is the textbook implicit QL algorithm for symmetric           */
+/* tridiagonal matrices (Bowdler, Martin, Reinsch and Wilkinson, "The QR    */
+/* and QL algorithms for symmetric matrices", Numer. Math. 11 (1968), the   */
+/* procedure tql2 of the Handbook for Automatic Computation, vol. II); it   */
+/* was written from that published description.                            */
 /* ------------------------------------------------------------------------ */
 int oracle_tql(int64_t n, double *d, double *e, double *Z, int64_t ldz) {
   double *f = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));

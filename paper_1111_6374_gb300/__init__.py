@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
                 ("wait_limit", ctypes.c_int32), ("start_block", ctypes.c_void_p), ("start_weights", ctypes.c_void_p),
                 ("start_cols", ctypes.c_int64), ("ld_start", ctypes.c_int64), ("filter_cut", ctypes.c_double),
                 ("filter_edge", ctypes.c_double), ("filter_degree", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("mixed", ctypes.c_int32), ("graph", ctypes.c_int32), ("max_ctas", ctypes.c_int32)]
+                ("mixed", ctypes.c_int32), ("graph", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
+                ("block_start", ctypes.c_int32)]
 
 
 class Problem(ctypes.Structure):
@@ -69,7 +70,9 @@ class Info(ctypes.Structure):
                [("diag_launches", ctypes.c_int64), ("diag_ms", ctypes.c_double), ("tnorm", ctypes.c_double),
                 ("filter_matvecs", ctypes.c_int64), ("slice_ms", ctypes.c_double)] + \
                [(f, ctypes.c_int64) for f in ("block_steps", "refine_iters")] + \
-               [(f, ctypes.c_double) for f in ("ms_block_lanczos", "ms_refine")]
+               [(f, ctypes.c_double) for f in ("ms_block_lanczos", "ms_refine")] + \
+               [(f, ctypes.c_int64) for f in ("refine_stop", "refine_fallback", "symm32_launches")] + \
+               [("symm32_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -116,8 +119,9 @@ def load(build_if_missing: bool = True):
         "gsyeig_mlp_adam": ([vp, vp, vp, vp, i64, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_float, vp], i32),
         "gsyeig_ws_features": ([i64, vp, vp, dp, vp, vp, vp], i32),
-        "gsyeig_ws_targets": ([i64, vp, vp, vp, i64, vp, vp], i32),
-        "gsyeig_ws_decode": ([i64, vp, vp, dp, dp, vp, vp, vp], i32),
+        "gsyeig_ws_align": ([i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp], i32),
+        "gsyeig_ws_coef_targets": ([i64, i64, vp, i64, vp, i64, vp, i64, dp, dp, vp, vp], i32),
+        "gsyeig_ws_extrapolate": ([i64, i64, vp, i64, vp, i64, vp, dp, dp, vp, i64, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

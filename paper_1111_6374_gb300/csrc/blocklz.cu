@@ -222,6 +222,35 @@ __global__ void k_gather_cols(int64_t n, int64_t cnt, const int *__restrict__ id
   }
 }
 
+// out[0] = max_c sum_i |M(i, c)| (the 1-norm; the infinity norm of a
+// symmetric M), one CTA per column, combined by atomicMax on the bits of
+// the non-negative sums; out[0] must start at 0
+__global__ void k_norm1(int64_t n, const double *__restrict__ M, int64_t ldm, unsigned long long *out) {
+  __shared__ double red[32];
+  const double *col = M + (int64_t)blockIdx.x * ldm;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += fabs(col[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) v += red[k];
+    atomicMax(out, (unsigned long long)__double_as_longlong(v));
+  }
+}
+
+// M(i, j) *= theta_i^pa theta_j^pb (m x m, theta > 0)
+__global__ void k_scale_by_powers(int64_t m, double *__restrict__ M, int64_t ldm, const double *__restrict__ theta,
+                                  double pa, double pb) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % m, j = idx / m;
+    M[i + j * ldm] *= pow(theta[i], pa) * pow(theta[j], pb);
+  }
+}
+
 unsigned g1(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 4096)); }
 
 }  // namespace
@@ -326,6 +355,22 @@ int gather_cols(cudaStream_t st, int64_t n, int64_t cnt, const int *idx, const d
                 int64_t ldd) {
   if (cnt <= 0) return GSYEIG_SUCCESS;
   k_gather_cols<<<g1(n * cnt), 256, 0, st>>>(n, cnt, idx, src, lds, dst, ldd);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int scale_by_powers(cudaStream_t st, int64_t m, double *M, int64_t ldm, const double *theta, double pa, double pb) {
+  if (m <= 0) return GSYEIG_SUCCESS;
+  k_scale_by_powers<<<g1(m * m), 256, 0, st>>>(m, M, ldm, theta, pa, pb);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int mat_norm1(cudaStream_t st, int64_t n, const double *M, int64_t ldm, double *out) {
+  GS_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  k_norm1<<<(unsigned)n, 256, 0, st>>>(n, M, ldm, reinterpret_cast<unsigned long long *>(out));
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;

@@ -7,17 +7,19 @@
 //    "no-swizzle K-major" core-matrix layout (8 rows x 16 bytes per core
 //    matrix, K-adjacent cores 128 B apart, row-adjacent cores 256 B apart),
 //    grouped so that one K stage (32 k: two k16 blocks of all 7 slices) of a
-//    128-row A block (56 KB) or a 64-row B block (28 KB) is one contiguous
+//    128-row A block (56 KB) or a 32-row B block (14 KB) is one contiguous
 //    run: each stage is brought in by a single cp.async.bulk per operand into
-//    a 2-deep ring, completing on an mbarrier (no tensor map needed).
-//  * Persistent CTAs (one per SM) walk the 128 x 64 tiles of C with
+//    a 3-deep ring, completing on an mbarrier (no tensor map needed).
+//  * Persistent CTAs (one per SM) walk the 128 x 32 tiles of C with
 //    warp-specialised roles: a producer lane, an MMA lane and 16 epilogue
 //    warps.  One thread issues tcgen05.mma.kind::f16 (bf16 x bf16 -> fp32,
 //    M = 128, K = 16); the accumulator of level d lives in TMEM columns
-//    [64 d, 64 d + 64) (7 levels, 448 columns, 512 allocated).  The 28 digit
-//    products of a k16 block go out as 10 MMAs of N = 64..256 (a run of B
-//    slices against one A slice fills a run of levels); tcgen05.commit
-//    releases the stage buffer.
+//    [32 d, 32 d + 32) of one of two sets (columns 0 and 256; 7 levels, 224
+//    columns each, 512 allocated).  The 28 digit products of a k16 block go
+//    out as 7 MMAs of N = 32..224 (the B slices 0..6-p against A slice p
+//    fill levels p..6); tcgen05.commit releases the stage buffer.
+//  * Consecutive K chunks alternate between the two sets, so the epilogue
+//    folds one chunk out of TMEM while the MMAs of the next one run.
 //  * K up to 512 per call, in exact chunks of K = 128: after each chunk the
 //    epilogue (warp w reads TMEM lane quarter w % 4, a quarter of the
 //    columns each) reads the 7 level sums with tcgen05.ld, recombines them
@@ -38,17 +40,19 @@ namespace {
 
 using slicing::S;
 using slicing::EXP_NONE;
-constexpr int UM = 128, UN = 64, UKS = 32;  // tile rows, tile cols, K per stage
+constexpr int UM = 128, UN = 32, UKS = 32;  // tile rows, tile cols, K per stage
 constexpr int KB2 = UKS / 16;                // k16 blocks per stage
 constexpr int KPAD = 32;                     // K padding of the digit planes
 constexpr int A_K16_BYTES = UM * 16 * 2;     // one slice, one k16 block: 4096
-constexpr int B_K16_BYTES = UN * 16 * 2;     // 2048
+constexpr int B_K16_BYTES = UN * 16 * 2;     // 1024
 constexpr int A_STAGE = KB2 * S * A_K16_BYTES;  // 57344
-constexpr int B_STAGE = KB2 * S * B_K16_BYTES;  // 28672
-constexpr int NBUF = 2;
+constexpr int B_STAGE = KB2 * S * B_K16_BYTES;  // 14336
+constexpr int NBUF = 3;
 constexpr int CH_STAGES = 128 / UKS;  // K stages per exact chunk (level sums exact for K <= 128)
 constexpr int UMMA_MAX_K = 512;
 constexpr int TMEM_COLS = 512;
+constexpr int SET_COLS = 256;  // two accumulator sets of 7 levels x UN columns, at columns 0 and 256
+constexpr int NGROUP = S;      // MMAs per k16 block
 constexpr uint32_t SPIN_LIMIT = 1u << 24;
 
 int num_sms() { return num_sms_cached(); }
@@ -115,21 +119,16 @@ __host__ __device__ constexpr uint32_t instr_desc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
 }
 
-// The 28 digit products (p, q), p + q <= 6, as 10 MMAs: B slices q0..q0+nq-1
-// lie back to back in shared memory (one 64-row block each) and level d's
-// accumulator is TMEM columns [64 d, 64 d + 64), so A_p times the
-// (64 nq)-row block of those slices (N = 64 nq <= 256) writes levels
-// p + q0 .. p + q0 + nq - 1 in one instruction.  The two MMAs of p = 0
-// cover every level once: they start a chunk's accumulators.
+// The 28 digit products (p, q), p + q <= 6, as 7 MMAs: the B slices
+// 0..6 - p lie back to back in shared memory (one UN-row block each) and
+// level d's accumulator is TMEM columns [UN d, UN d + UN) of a set, so A_p
+// times the (UN (7 - p))-row block of those slices (N = UN (7 - p) <= 224)
+// writes levels p .. 6 in one instruction.  The MMA of p = 0 covers every
+// level once: it starts a chunk's accumulators.
 struct MmaGroup {
   int p, q0, nq;
 };
-__host__ __device__ constexpr MmaGroup mma_group(int i) {
-  return i == 0 ? MmaGroup{0, 0, 4} : i == 1 ? MmaGroup{0, 4, 3} : i == 2 ? MmaGroup{1, 0, 4}
-       : i == 3 ? MmaGroup{1, 4, 2} : i == 4 ? MmaGroup{2, 0, 4} : i == 5 ? MmaGroup{2, 4, 1}
-       : i == 6 ? MmaGroup{3, 0, 4} : i == 7 ? MmaGroup{4, 0, 3} : i == 8 ? MmaGroup{5, 0, 2}
-                : MmaGroup{6, 0, 1};
-}
+__host__ __device__ constexpr MmaGroup mma_group(int i) { return MmaGroup{i, 0, S - i}; }
 
 __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -239,19 +238,21 @@ __device__ __forceinline__ double i128_to_double(int32_t h, uint64_t l, int e2, 
 // (M / 128) x (N / 64) grid of C (column-major in m), tiles outside the
 // triangle of a TRI mode skipped by every role alike.
 //   warp 16 (one lane): producer -- bulk copies of each K stage into a
-//       2-deep ring, released by the MMA commits;
-//   warp 17 (one lane): MMA issuer -- waits for the epilogue to have drained
-//       the accumulators of the previous tile, then 28 x 2 MMAs per stage;
-//   warps 0-15: epilogue -- read the 7 level sums of 16 elements each from
-//       TMEM, fold them into 128-bit integers in registers, hand TMEM back
-//       (the next tile's MMAs start), then update C from the registers.
+//       3-deep ring, released by the MMA commits;
+//   warp 17 (one lane): MMA issuer -- before each K chunk waits for the
+//       epilogue to have folded the chunk two before (the same accumulator
+//       set), then 7 x 2 MMAs per stage;
+//   warps 0-15: epilogue -- read the 7 level sums of 8 elements each from
+//       TMEM, fold them into 128-bit integers in registers, hand the set back
+//       (the MMAs of the chunk after next may start), and after a tile's
+//       last chunk update C from the registers.
 // Every wait is bounded; a wait that runs out sets s_fail, every role leaves
 // its loop, the MMA issuer waits (bounded) for its own MMAs and thread 0 for
 // the producer's copies before TMEM is freed.
 constexpr int EPI_WARPS = 16;
 constexpr int PRODUCER_WARP = EPI_WARPS, MMA_WARP = EPI_WARPS + 1;
 constexpr int UMMA_THREADS = (EPI_WARPS + 2) * 32;
-constexpr int EPI_COLS = UN / (EPI_WARPS / 4);  // columns of a tile per epilogue warp (16)
+constexpr int EPI_COLS = UN / (EPI_WARPS / 4);  // columns of a tile per epilogue warp (8)
 
 // Exact integer value of a level sum (an integer-valued fp32, |x| < 2^24).
 __device__ __forceinline__ int32_t lvl(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
@@ -296,9 +297,10 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
   unsigned char *bufA = smem;                   // NBUF x A_STAGE
   unsigned char *bufB = smem + NBUF * A_STAGE;  // NBUF x B_STAGE
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NBUF * (A_STAGE + B_STAGE));
-  uint64_t *full = bars, *empty = bars + NBUF, *acc_full = bars + 2 * NBUF, *acc_empty = acc_full + 1,
-           *fin = acc_full + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NBUF + 3);
+  // per accumulator set: acc_full (the chunk's MMAs are done), acc_empty (the epilogue has folded it)
+  uint64_t *full = bars, *empty = bars + NBUF, *acc_full = bars + 2 * NBUF, *acc_empty = acc_full + 2,
+           *fin = acc_full + 4;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NBUF + 5);
   __shared__ int s_fail;
   __shared__ int64_t s_issued;  // stages whose bulk copies were issued
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -309,8 +311,10 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, EPI_WARPS);
+    for (int i = 0; i < 2; i++) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], EPI_WARPS);
+    }
     mbar_init(fin, 1);
     s_fail = 0;
     s_issued = 0;
@@ -350,9 +354,12 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     }
   } else if (warp == MMA_WARP) {
     if (lane == 0) {
-      const uint32_t idesc[5] = {0u, instr_desc(UN), instr_desc(2 * UN), instr_desc(3 * UN), instr_desc(4 * UN)};
+      uint32_t idesc[S + 1];
+#pragma unroll
+      for (int q = 0; q <= S; q++) idesc[q] = instr_desc(q > 0 ? q * UN : UN);
       int64_t it = 0;
-      int64_t fc = 0;  // chunks handed to the epilogue
+      int64_t fc = 0;  // chunks issued
+      uint32_t set_base = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
         int64_t m0, n0;
@@ -361,11 +368,13 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
           const int b = (int)(it % NBUF);
           const bool first = (ks % CH_STAGES) == 0;  // first stage of an exact K chunk
           if (first) {
-            // the epilogue has folded the previous chunk's accumulators out of TMEM
-            if (fc > 0 && !mbar_wait(acc_empty, (uint32_t)((fc - 1) & 1), spin)) {
+            // this chunk's set (fc & 1) was folded out of TMEM by the epilogue (chunk fc - 2)
+            const int set = (int)(fc & 1);
+            if (fc >= 2 && !mbar_wait(&acc_empty[set], (uint32_t)(((fc >> 1) - 1) & 1), spin)) {
               ok = false;
               break;
             }
+            set_base = (uint32_t)(set * SET_COLS);
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
           }
           if (failed(&s_fail) || !mbar_wait(&full[b], (uint32_t)((it / NBUF) & 1), spin)) {
@@ -377,16 +386,16 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
 #pragma unroll
           for (int kb2 = 0; kb2 < KB2; kb2++)
 #pragma unroll
-            for (int gq = 0; gq < 10; gq++) {
+            for (int gq = 0; gq < NGROUP; gq++) {
               const MmaGroup gr = mma_group(gq);
               const uint64_t ad = smem_desc(a0 + (uint32_t)((kb2 * S + gr.p) * A_K16_BYTES), 128, 256);
               const uint64_t bd = smem_desc(b0 + (uint32_t)((kb2 * S + gr.q0) * B_K16_BYTES), 128, 256);
               const uint32_t acc = (first && kb2 == 0 && gr.p == 0) ? 0u : 1u;
-              umma(tmem + (uint32_t)((gr.p + gr.q0) * UN), ad, bd, idesc[gr.nq], acc);
+              umma(tmem + set_base + (uint32_t)((gr.p + gr.q0) * UN), ad, bd, idesc[gr.nq], acc);
             }
           umma_commit(&empty[b]);
           if ((ks % CH_STAGES) == CH_STAGES - 1 || ks == nks - 1) {
-            umma_commit(acc_full);
+            umma_commit(&acc_full[fc & 1]);
             fc++;
           }
         }
@@ -399,7 +408,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     }
   } else {
     // epilogue: warp w reads TMEM lane quarter w % 4 (rows 32 (w % 4) + lane)
-    // and columns [16 (w / 4), 16 (w / 4) + 16) of every level
+    // and columns [8 (w / 4), 8 (w / 4) + 8) of every level
     const int quarter = warp & 3, cgroup = warp >> 2;
     const bool neg_alpha = alpha < 0.0;
     const int ea2 = (alpha == 0.0) ? 0 : (int)((__double_as_longlong(fabs(alpha)) >> 52) & 0x7FF) - 1023;
@@ -428,7 +437,8 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
       for (int64_t ch = 0; ch < nch; ch++, fc++) {
         // the warp decides together (the TMEM loads and shuffles below are
         // .sync.aligned: no lane may leave on its own)
-        const bool got = mbar_wait(acc_full, (uint32_t)(fc & 1), spin);
+        const int set = (int)(fc & 1);
+        const bool got = mbar_wait(&acc_full[set], (uint32_t)((fc >> 1) & 1), spin);
         if (!__all_sync(0xffffffffu, got)) {
           if (lane == 0) atomicExch(&s_fail, 1);
           ok = false;
@@ -444,7 +454,8 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
           uint32_t v[S][4];
 #pragma unroll
           for (int d = 0; d < S; d++)
-            tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * UN + cgroup * EPI_COLS + c0), v[d]);
+            tmem_ld4(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(set * SET_COLS + d * UN + cgroup * EPI_COLS + c0),
+                     v[d]);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
           for (int d = 0; d < S; d++)
@@ -459,7 +470,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         // TMEM is free for the next chunk's MMAs
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sptr(acc_empty)) : "memory");
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sptr(&acc_empty[set])) : "memory");
       }
       if (!ok) break;
       const bool row_ok = gi < g.M;  // (no early exit: the warp shuffles below need every lane)

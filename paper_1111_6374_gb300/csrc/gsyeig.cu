@@ -59,6 +59,8 @@ struct gsyeig_ctx {
   DevBuf uinvO;           // inverses of the outer diagonal blocks and the outer panel staging
   DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts, arrow;
   DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
+  cudaStream_t cp = nullptr;  // host-pointer calls: the copy of the matrix needed second
+  cudaEvent_t cp_ev = nullptr;
   DevBuf pA, pB;          // working copies when opts.preserve_inputs
   DevBuf vA, vB, vws;     // originals and workspace of opts.verify
   DevBuf gemm_ws;         // slices of the tensor-core GEMM
@@ -68,7 +70,7 @@ struct gsyeig_ctx {
   DevBuf tmin;            // smallest eigenvalue of the final projected matrix
   DevBuf wstart;          // start-block construction and Chebyshev filter vectors
   // mixed precision: fp32 operator and staging, block basis, projected matrices, refinement blocks
-  DevBuf mx_op, mx_w, mx_z, mx_V, mx_Zd, mx_H, mx_part, mx_T, mx_small, mx_Sb, mx_CSb, mx_tmp, mx_fw, mx_P;
+  DevBuf mx_op, mx_w, mx_z, mx_V, mx_Zd, mx_H, mx_part, mx_T, mx_small, mx_Sb, mx_CSb, mx_tmp, mx_fw, mx_ones;
   DfOperator op, opL;
   bool use_df = false;
   bool ki = false;        // the operator is U^-T G U^-1 applied implicitly (variant KI)
@@ -123,6 +125,8 @@ struct ProfScope {
     info->diag_launches = l[PROF_DIAG];
     info->diag_ms = ms[PROF_DIAG];
     info->slice_ms = ms[PROF_SLICE];
+    info->symm32_launches = l[PROF_SYMV32];
+    info->symm32_ms = ms[PROF_SYMV32];
   }
   ~ProfScope() {
     if (on) {
@@ -456,8 +460,6 @@ int lanczos_run(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_
 
   const bool thick = (h->opts.qr_restart == 0);
   int64_t ka = 0;                                               // arrow rows of M (thick restart)
-  const int64_t wf = (which == GSYEIG_LARGEST) ? m - s : 0;  // first wanted index among the m Ritz values
-  const int64_t kfirst = (which == GSYEIG_LARGEST) ? m - k : 0;  // first kept index (thick restart)
   const int64_t woff = (thick && which == GSYEIG_LARGEST) ? k - s : 0;  // wanted columns within S
   const double *shifts = (which == GSYEIG_LARGEST) ? h->theta.d() : h->theta.d() + k;
   const int dir = (which == GSYEIG_LARGEST) ? -1 : 1;  // nearest-to-wanted shift first
@@ -739,31 +741,49 @@ int cholqr2(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t b, double *Z, i
 // through an FP64 block refinement (LOBPCG: Rayleigh-Ritz on [X, R, P],
 // C products on the FP64-accurate GEMM engine) until the s wanted residuals
 // meet tol ||C||.  Ritz values ascending into theta_out, vectors into Y.
+//
+// With warm = true (opts.block_start and a start block of at least s
+// columns) the fp32 stage is skipped: the refinement starts from the start
+// block mapped into the operator's space by the factor F (F X0), with
+// max(8, s/4) random guard columns, and ||C|| is bounded by its 1-norm.
+//
+// With stage_out != NULL (opts.mixed = 1) the function stops after the fp32
+// stage: *stage_out = the s wanted Ritz vectors of the band matrix (n x s,
+// ld n, in the handle's workspace), the start of the FP64 Lanczos stage.
 int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_t s, int which, double *theta_out,
-                  double *Y, int64_t ldy, gsyeig_info *info, double *ms_ke3) {
+                  double *Y, int64_t ldy, gsyeig_info *info, double *ms_ke3, const double *F = nullptr,
+                  int64_t ldf = 0, const double **stage_out = nullptr) {
   cudaStream_t st = h->st;
   constexpr int BK = 16;
-  int64_t mb = h->opts.krylov_dim > 0 ? h->opts.krylov_dim : std::max<int64_t>(5 * s, s + 64);
+  const gsyeig_opts &o = h->opts;
+  const bool warm = o.block_start == 1 && o.start_block && o.start_cols >= s;
+  // the fp32 stage feeding the FP64 Lanczos (stage_out) needs approximations,
+  // not converged pairs: a smaller block Krylov space by default
+  int64_t mb = o.krylov_dim > 0 ? o.krylov_dim : std::max<int64_t>((stage_out ? 3 : 5) * s, s + 64);
   mb = std::min<int64_t>(ceil_div(mb, BK) * BK, (n / BK) * BK - BK);
-  const int64_t g = std::max<int64_t>(16, s / 8);
-  const int64_t k = std::min<int64_t>(s + g, mb - BK);
-  if (n < 8 * BK || mb < 2 * BK || s >= k || 3 * k >= n) return GSYEIG_NOT_SUPPORTED;
+  const int64_t g = warm ? std::max<int64_t>(8, s / 4) : std::max<int64_t>(16, s / 8);
+  const int64_t k = warm ? std::min<int64_t>(o.start_cols + g, n / 4) : std::min<int64_t>(s + g, mb - BK);
+  if (warm && (o.ld_start < n || k <= s || 3 * k >= n)) return GSYEIG_NOT_SUPPORTED;
+  if (!warm && (n < 8 * BK || mb < 2 * BK || s >= k || 3 * k >= n)) return GSYEIG_NOT_SUPPORTED;
+  if (warm && stage_out) return GSYEIG_NOT_SUPPORTED;
+  if (warm) mb = BK;  // no fp32 stage
   const int64_t nblk = mb / BK;
   // ---- workspace
-  GS_TRY(h->mx_op.ensure(f32_operator_bytes(n)));
-  GS_TRY(h->mx_w.ensure(f32_block_bytes(n)));
-  GS_TRY(h->mx_z.ensure(f32_block_bytes(n)));
+  if (!warm) {
+    GS_TRY(h->mx_op.ensure(f32_operator_bytes(n)));
+    GS_TRY(h->mx_w.ensure(f32_block_bytes(n)));
+    GS_TRY(h->mx_z.ensure(f32_block_bytes(n)));
+  }
   GS_TRY(h->mx_V.ensure((size_t)n * (mb + BK) * sizeof(double)));
   GS_TRY(h->mx_Zd.ensure((size_t)n * BK * sizeof(double)));
   GS_TRY(h->mx_H.ensure((size_t)2 * (mb + BK) * BK * sizeof(double)));
   GS_TRY(h->mx_part.ensure(ts_part_doubles(n, mb + BK) * sizeof(double)));
   GS_TRY(h->mx_T.ensure((size_t)mb * mb * sizeof(double) + 64));
   const int64_t zrows = std::max<int64_t>(mb, 3 * k);
-  GS_TRY(h->mx_small.ensure(((size_t)9 * k * k + (size_t)zrows * k + 5 * k + 64) * sizeof(double)));
+  GS_TRY(h->mx_small.ensure(((size_t)12 * k * k + (size_t)zrows * k + 5 * k + 64) * sizeof(double)));
   GS_TRY(h->mx_Sb.ensure((size_t)n * 3 * k * sizeof(double)));
   GS_TRY(h->mx_CSb.ensure((size_t)n * 3 * k * sizeof(double)));
   GS_TRY(h->mx_tmp.ensure((size_t)n * 4 * k * sizeof(double)));
-  GS_TRY(h->mx_P.ensure((size_t)n * 2 * k * sizeof(double)));
   SmallFactor sf;
   GS_TRY(small_factor(h, 2 * k, sf));
   F32Operator op;
@@ -788,18 +808,37 @@ int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int6
     }
   } evg{ev0, ev1, ev2};
   GS_CUDA(cudaEventRecord(ev0, st));
+  GemmContext *gc0 = current_gemm();
+  int64_t blocks = 0;
+  double cnorm = 0.0;
+  int rc = GSYEIG_SUCCESS;
+  if (warm) {
+    // ---- the caller's block, mapped by F, plus random guard columns, orthonormal
+    for (int64_t c = 0; c < o.start_cols; c++) {
+      const double *xc = o.start_block + (size_t)c * o.ld_start;
+      if (F) GS_TRY(lz_trmv_upper(st, n, F, ldf, xc, Sb + (size_t)c * n));
+      else GS_CUDA(cudaMemcpyAsync(Sb + (size_t)c * n, xc, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    for (int64_t c = o.start_cols; c < k; c++) GS_TRY(lz_random(st, n, o.seed, 3000 + (uint64_t)c, Sb + (size_t)c * n));
+    GS_TRY(col_norms(st, n, k, Sb, n, sf.norms));
+    GS_TRY(scale_cols(st, n, k, Sb, n, sf.norms));
+    rc = cholqr2(h, st, n, k, Sb, n, nullptr, 0, nullptr, sf, tmp, part);
+    if (rc != GSYEIG_SUCCESS) return rc == GSYEIG_NOT_SPD ? GSYEIG_NOT_SUPPORTED : rc;
+    GS_TRY(mat_norm1(st, n, C, ldc, cn));
+    GS_CUDA(cudaMemcpyAsync(&cnorm, cn, sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+  } else {
   // ---- fp32 operator and a random orthonormal start block
   GS_TRY(f32_operator_build(st, n, C, ldc, op));
   for (int c = 0; c < BK; c++) GS_TRY(lz_random(st, n, h->opts.seed, 2000 + (uint64_t)c, V + (size_t)c * n));
   GS_CUDA(cudaMemsetAsync(T, 0, (size_t)mb * mb * sizeof(double), st));
   current_gemm() = nullptr;  // small products in FP64
-  int rc = cholqr2(h, st, n, BK, V, n, nullptr, 0, nullptr, sf, tmp, part);
+  rc = cholqr2(h, st, n, BK, V, n, nullptr, 0, nullptr, sf, tmp, part);
   if (rc != GSYEIG_SUCCESS) {
     current_gemm() = gc;
     return rc;
   }
   // ---- block Lanczos: Z = C V_j (fp32), CGS2 in FP64, Z = V_{j+1} B_j
-  int64_t blocks = 0;
   for (int64_t j = 0; j < nblk; j++) {
     double *Vj = V + (size_t)j * BK * n;
     GS_TRY(f32_symm(st, op, Vj, n, Zd, n));
@@ -826,7 +865,6 @@ int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int6
   }
   GS_TRY(sym_avg(st, mb, T, mb));
   GS_TRY(inf_norm(st, mb, T, mb, cn));
-  double cnorm = 0.0;
   GS_CUDA(cudaMemcpyAsync(&cnorm, cn, sizeof(double), cudaMemcpyDeviceToHost, st));
   // ---- the k wanted Ritz pairs of the band matrix, X = V S
   {
@@ -835,20 +873,38 @@ int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int6
   }
   current_gemm() = gc;
   GS_TRY(dgemm(st, false, false, n, k, mb, 1.0, V, n, Zs, mb, 0.0, Sb, n));
+  }
+  (void)gc0;
   GS_CUDA(cudaEventRecord(ev1, st));
-  // ---- FP64 block refinement on C (LOBPCG with soft locking: columns whose
-  // residual already meets the tolerance leave the search space, so that
-  // the normalised search directions never magnify rounding)
-  double *X = Sb, *CX = CSb, *Pb = h->mx_P.d(), *CPb = Pb + (size_t)n * k;
+  if (stage_out) {
+    *stage_out = Sb + (size_t)((which == GSYEIG_LARGEST) ? k - s : 0) * n;
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (info) {
+      info->block_steps = blocks;
+      info->ms_block_lanczos = elapsed(ev0, ev1);
+      info->matvecs = blocks * BK;
+    }
+    return GSYEIG_SUCCESS;
+  }
+  // ---- FP64 block refinement on C: LOBPCG (Knyazev 2001) with soft locking
+  // (columns whose residual meets the tolerance leave the search space) on an
+  // orthonormal basis S = [X, P, W] chosen as Hetmaniuk and Lehoucq (2006)
+  // do: the new directions W are made orthonormal against [X, P] before
+  // their product with C is taken, and P is chosen in the coordinates of S
+  // (P = S Q, C P = (C S) Q with Q orthonormal), so that no carried product
+  // passes through the inverse of an ill-conditioned factor.
+  double *X = Sb, *CX = CSb;
   int *idx = reinterpret_cast<int *>(res + k);
+  double *Qs = res + 2 * k;  // ms x na coordinates of the next P
   GS_TRY(dgemm(st, false, false, n, k, n, 1.0, C, ldc, X, n, 0.0, CX, n));
   GS_TRY(column_dots(st, n, k, X, n, CX, n, thv));  // Rayleigh quotients of the columns
   const int64_t w0 = (which == GSYEIG_LARGEST) ? k - s : 0;  // wanted columns w0..w0+s-1
   const double tol = h->opts.tol;
-  std::vector<double> hres(k);
+  std::vector<double> hres(k), hist;
   std::vector<int> act;
-  int64_t iters = 0, products = k;
-  bool have_p = false, done = false;
+  int64_t iters = 0, products = k, qr_fail = 0, stop = 0;
+  int64_t np = 0;  // columns of P, stored after X in S
+  bool done = false;
   for (; iters < 60; iters++) {
     double *Rf = tmp;  // the k residuals
     GS_TRY(block_resid(st, n, k, CX, X, n, thv, Rf));
@@ -861,58 +917,92 @@ int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int6
       done = true;
       break;
     }
+    // the rate over the last 4 steps predicts the steps still needed; when
+    // they do not fit in the limit (small relative gaps at the wanted end),
+    // stop now and leave the pairs to the FP64 Lanczos stage
+    hist.push_back(mx);
+    if (iters >= 6) {
+      const double r = std::pow(mx / hist[iters - 4], 0.25);
+      if (!(r < 1.0) || (double)iters + std::log(tol * cnorm / mx) / std::log(r) > 60.0) {
+        stop = 2;
+        break;
+      }
+    }
     act.clear();
     for (int64_t i = 0; i < k; i++)
       if (hres[i] > tol * cnorm) act.push_back((int)i);
     const int64_t na = (int64_t)act.size();
     ProfRegion pr(st, PROF_RESTART);
     GS_CUDA(cudaMemcpyAsync(idx, act.data(), (size_t)na * sizeof(int), cudaMemcpyHostToDevice, st));
-    double *W = Sb + (size_t)k * n, *CW = CSb + (size_t)k * n;
-    int64_t wb = 0;
-    rc = GSYEIG_NOT_SPD;
-    for (int attempt = 0; attempt < 2 && rc != GSYEIG_SUCCESS; attempt++) {
-      if (attempt == 1) {
-        if (!have_p) break;
-        have_p = false;  // [R, P] numerically dependent: restart the directions from R
+    const int64_t kp = k + np;  // [X, P], orthonormal
+    double *W = Sb + (size_t)kp * n, *CW = CSb + (size_t)kp * n;
+    GS_TRY(gather_cols(st, n, na, idx, Rf, n, W, n));
+    // W against [X, P], then orthonormal (Cholesky QR twice); the factor
+    // R^-1 of nearly dependent residuals magnifies what is left of [X, P]
+    // in W, so the projection and the Cholesky QR are repeated on the
+    // well-conditioned result
+    rc = GSYEIG_SUCCESS;
+    for (int round = 0; round < 2 && rc == GSYEIG_SUCCESS; round++) {
+      for (int pass = 0; pass < 2 - round; pass++) {
+        GS_TRY(dgemm(st, true, false, kp, na, n, 1.0, Sb, n, W, n, 0.0, Hs, kp));
+        GS_TRY(dgemm(st, false, false, n, na, kp, -1.0, Sb, n, Hs, kp, 1.0, W, n));
       }
-      GS_TRY(gather_cols(st, n, na, idx, Rf, n, W, n));
-      GS_TRY(dgemm(st, false, false, n, na, n, 1.0, C, ldc, W, n, 0.0, CW, n));
-      products += na;
-      wb = na;
-      if (have_p) {
-        GS_TRY(copy_block(st, n, k, Pb, n, W + (size_t)na * n, n));
-        GS_TRY(copy_block(st, n, k, CPb, n, CW + (size_t)na * n, n));
-        wb += k;
+      if (round == 0) {
+        GS_TRY(col_norms(st, n, na, W, n, sf.norms));
+        GS_TRY(scale_cols(st, n, na, W, n, sf.norms));
       }
-      // W against X (twice), C W following the same combinations
-      for (int pass = 0; pass < 2; pass++) {
-        GS_TRY(dgemm(st, true, false, k, wb, n, 1.0, X, n, W, n, 0.0, Hs, k));
-        GS_TRY(dgemm(st, false, false, n, wb, k, -1.0, X, n, Hs, k, 1.0, W, n));
-        GS_TRY(dgemm(st, false, false, n, wb, k, -1.0, CX, n, Hs, k, 1.0, CW, n));
-      }
-      GS_TRY(col_norms(st, n, wb, W, n, sf.norms));
-      GS_TRY(scale_cols(st, n, wb, W, n, sf.norms));
-      GS_TRY(scale_cols(st, n, wb, CW, n, sf.norms));
-      rc = cholqr2(h, st, n, wb, W, n, CW, n, nullptr, sf, tmp + (size_t)k * n, part);
+      rc = cholqr2(h, st, n, na, W, n, nullptr, 0, nullptr, sf, tmp + (size_t)k * n, part);
       if (rc != GSYEIG_SUCCESS && rc != GSYEIG_NOT_SPD) return rc;
     }
-    if (rc != GSYEIG_SUCCESS) break;  // no new directions: keep the current pairs
-    // Rayleigh-Ritz on S = [X, W]
-    const int64_t ms = k + wb;
+    if (rc != GSYEIG_SUCCESS) {  // the residuals are numerically dependent: keep the current pairs
+      qr_fail++;
+      stop = 1;
+      break;
+    }
+    GS_TRY(dgemm(st, false, false, n, na, n, 1.0, C, ldc, W, n, 0.0, CW, n));
+    products += na;
+    // Rayleigh-Ritz on S = [X, P, W]
+    const int64_t ms = kp + na;
     GS_TRY(dgemm(st, true, false, ms, ms, n, 1.0, Sb, n, CSb, n, 0.0, Hs, ms));
     GS_TRY(sym_avg(st, ms, Hs, ms));
     GS_TRY(small_syev(h, Hs, ms, k, which, thv, Zs, ms));
-    // X <- S Z, C X <- C S Z, P <- W Z_W, C P <- C W Z_W
-    double *Xn = tmp, *Pn = tmp + (size_t)k * n, *CXn = tmp + (size_t)2 * k * n, *CPn = tmp + (size_t)3 * k * n;
+    // the next P: the active Ritz vectors' components outside the old X
+    // (the rows of Z below the first k), made orthonormal against Z in the
+    // coordinates of S; if they are numerically dependent, the next step
+    // goes without P
+    int64_t np_new = na;
+    GS_TRY(gather_cols(st, ms, na, idx, Zs, ms, Qs, ms));
+    GS_CUDA(cudaMemset2DAsync(Qs, (size_t)ms * sizeof(double), 0, (size_t)k * sizeof(double), (size_t)na, st));
+    rc = GSYEIG_SUCCESS;
+    for (int round = 0; round < 2 && rc == GSYEIG_SUCCESS; round++) {
+      for (int pass = 0; pass < 2 - round; pass++) {
+        GS_TRY(dgemm(st, true, false, k, na, ms, 1.0, Zs, ms, Qs, ms, 0.0, Hs, k));
+        GS_TRY(dgemm(st, false, false, ms, na, k, -1.0, Zs, ms, Hs, k, 1.0, Qs, ms));
+      }
+      if (round == 0) {
+        GS_TRY(col_norms(st, ms, na, Qs, ms, sf.norms));
+        GS_TRY(scale_cols(st, ms, na, Qs, ms, sf.norms));
+      }
+      rc = cholqr2(h, st, ms, na, Qs, ms, nullptr, 0, nullptr, sf, tmp, part);
+      if (rc != GSYEIG_SUCCESS && rc != GSYEIG_NOT_SPD) return rc;
+    }
+    if (rc != GSYEIG_SUCCESS) {
+      qr_fail++;
+      np_new = 0;
+    }
+    // X <- S Z, C X <- (C S) Z, P <- S Q, C P <- (C S) Q
+    double *Xn = tmp, *CXn = tmp + (size_t)k * n, *Pn = tmp + (size_t)2 * k * n, *CPn = tmp + (size_t)3 * k * n;
     GS_TRY(dgemm(st, false, false, n, k, ms, 1.0, Sb, n, Zs, ms, 0.0, Xn, n));
     GS_TRY(dgemm(st, false, false, n, k, ms, 1.0, CSb, n, Zs, ms, 0.0, CXn, n));
-    GS_TRY(dgemm(st, false, false, n, k, wb, 1.0, W, n, Zs + k, ms, 0.0, Pn, n));
-    GS_TRY(dgemm(st, false, false, n, k, wb, 1.0, CW, n, Zs + k, ms, 0.0, CPn, n));
+    if (np_new > 0) {
+      GS_TRY(dgemm(st, false, false, n, np_new, ms, 1.0, Sb, n, Qs, ms, 0.0, Pn, n));
+      GS_TRY(dgemm(st, false, false, n, np_new, ms, 1.0, CSb, n, Qs, ms, 0.0, CPn, n));
+      GS_TRY(copy_block(st, n, np_new, Pn, n, Sb + (size_t)k * n, n));
+      GS_TRY(copy_block(st, n, np_new, CPn, n, CSb + (size_t)k * n, n));
+    }
     GS_TRY(copy_block(st, n, k, Xn, n, X, n));
     GS_TRY(copy_block(st, n, k, CXn, n, CX, n));
-    GS_TRY(copy_block(st, n, k, Pn, n, Pb, n));
-    GS_TRY(copy_block(st, n, k, CPn, n, CPb, n));
-    have_p = true;
+    np = np_new;
   }
   // ke3: the s wanted pairs
   GS_CUDA(cudaEventRecord(ev2, st));
@@ -928,6 +1018,8 @@ int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int6
     info->keep = k;
     info->block_steps = blocks;
     info->refine_iters = iters;
+    info->breakdowns = qr_fail;      // Gram matrices of the search directions that were not definite
+    info->refine_stop = stop;        // 1: residuals numerically dependent, 2: too slow to converge
     info->ms_block_lanczos = elapsed(ev0, ev1);
     info->ms_refine = elapsed(ev1, ev2);
     info->tnorm = cnorm;
@@ -936,6 +1028,38 @@ int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int6
     info->max_ritz_estimate = cnorm > 0 ? mx / cnorm : mx;
   }
   return done ? GSYEIG_SUCCESS : GSYEIG_NO_CONVERGENCE;
+}
+
+// Inverse route (Section 3.1): the pairs of the pencil are x = L^-1 y /
+// sqrt(mu), so X^T B X = D^-1/2 Y^T C' Y D^-1/2 (D = diag(mu)), and any
+// defect of Y^T C' Y is divided by sqrt(mu_i mu_j): for a wide range of the
+// wanted mu (a lambda near zero) the Ritz vectors' B-orthonormality suffers.
+// This makes it exact to rounding before the back-transform: M = D^-1/2
+// (Y^T C' Y) D^-1/2 (C' stored full; products on the FP64-accurate engine),
+// M = R^T R, Y <- Y D^-1/2 R^-1 D^1/2, so that X^T B X = R^-T M R^-1 = I.
+// theta (device, s, positive) = the mu of the columns of Y.  A Gram matrix
+// that is not positive definite leaves Y as it was.
+int b_orthonormalise_inverse(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t s, const double *Cp, int64_t ldc,
+                             double *Y, int64_t ldy, const double *theta) {
+  GS_TRY(h->mx_tmp.ensure((size_t)n * s * sizeof(double)));
+  GS_TRY(h->mx_small.ensure((size_t)2 * s * s * sizeof(double)));
+  SmallFactor sf;
+  GS_TRY(small_factor(h, s, sf));
+  double *W = h->mx_tmp.d(), *M = h->mx_small.d(), *K = M + (size_t)s * s;
+  GS_TRY(dgemm(st, false, false, n, s, n, 1.0, Cp, ldc, Y, ldy, 0.0, W, n));
+  GS_TRY(dgemm(st, true, false, s, s, n, 1.0, Y, ldy, W, n, 0.0, M, s));
+  GS_TRY(sym_avg(st, s, M, s));
+  GS_TRY(scale_by_powers(st, s, M, s, theta, -0.5, -0.5));
+  GS_TRY(potrf_blocked(st, s, M, s, (int)std::min<int64_t>(128, s), sf.w));
+  int flag = 0;
+  GS_CUDA(cudaMemcpyAsync(&flag, sf.w.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  if (flag) return GSYEIG_SUCCESS;
+  GS_TRY(trtri_upper_blocked(st, s, M, s, K, s, (int)std::min<int64_t>(128, s), sf.w, true));
+  GS_TRY(scale_by_powers(st, s, K, s, theta, -0.5, 0.5));
+  GS_TRY(dgemm(st, false, false, n, s, s, 1.0, Y, ldy, K, s, 0.0, W, n));
+  GS_TRY(copy_block(st, n, s, W, n, Y, ldy));
+  return GSYEIG_SUCCESS;
 }
 
 int check_solve_args(int64_t lda, int64_t ldb, int64_t n, int64_t s, int which, const void *A, const void *B,
@@ -998,7 +1122,7 @@ int gsyeig_destroy(gsyeig_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
-  DevBuf *bufs[] = {&h->uinvO, &h->mx_P, &h->mx_op, &h->mx_w, &h->mx_z, &h->mx_V, &h->mx_Zd, &h->mx_H, &h->mx_part, &h->mx_T,
+  DevBuf *bufs[] = {&h->uinvO, &h->mx_ones, &h->mx_op, &h->mx_w, &h->mx_z, &h->mx_V, &h->mx_Zd, &h->mx_H, &h->mx_part, &h->mx_T,
                     &h->mx_small, &h->mx_Sb, &h->mx_CSb, &h->mx_tmp, &h->mx_fw, &h->wstart, &h->kinv, &h->dfopL, &h->kt, &h->tmin, &h->pA, &h->pB, &h->vA, &h->vB, &h->vws, &h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
                     &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
                     &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
@@ -1009,6 +1133,8 @@ int gsyeig_destroy(gsyeig_handle h) {
   for (gsyeig_ctx *sub : h->subs) gsyeig_destroy(sub);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
+  if (h->cp_ev) cudaEventDestroy(h->cp_ev);
+  if (h->cp) cudaStreamDestroy(h->cp);
   if (h->st) cudaStreamDestroy(h->st);
   delete h;
   return GSYEIG_SUCCESS;
@@ -1024,8 +1150,8 @@ int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
       o->preserve_inputs > 1 || o->verify < 0 || o->verify > 1 || o->implicit < 0 || o->implicit > 1 ||
       o->wait_limit < 0 || o->filter_degree < 0 || o->filter_degree > 64 || o->check_every < 0 ||
       o->start_cols < 0 || (o->start_block && o->start_cols > 0 && o->ld_start < 1) ||
-      (o->filter_degree > 0 && !(o->filter_cut != o->filter_edge)) || o->mixed < 0 || o->mixed > 1 ||
-      o->graph < 0 || o->graph > 1 || o->max_ctas < 0)
+      (o->filter_degree > 0 && !(o->filter_cut != o->filter_edge)) || o->mixed < 0 || o->mixed > 2 ||
+      o->graph < 0 || o->graph > 1 || o->max_ctas < 0 || o->block_start < 0 || o->block_start > 1)
     return -2;
   if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
   h->opts = *o;
@@ -1234,6 +1360,14 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   if (hostA != hostB || hostA != hostX) return -10;
   double *dA = A, *dB = B, *dX = X;
   int64_t dlda = lda, dldb = ldb, dldx = ldx;
+  // every return waits for a copy still in flight on the second stream (the
+  // caller may free its host buffer once the call returns)
+  struct CopyGuard {
+    cudaStream_t st = nullptr;
+    ~CopyGuard() {
+      if (st) cudaStreamSynchronize(st);
+    }
+  } copy_pending;
   GS_CUDA(cudaEventRecord(h->ev[0], st));
   if (hostA) {
     GS_TRY(h->hA.ensure((size_t)n * n * sizeof(double)));
@@ -1243,11 +1377,31 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     dB = h->hB.d();
     dX = h->hX.d();
     dlda = dldb = dldx = n;
-    GS_CUDA(cudaMemcpy2DAsync(dA, n * sizeof(double), A, lda * sizeof(double), n * sizeof(double), n,
+    // the matrix factored first (A on the inverse route, else B) on the
+    // solve's stream; the other on a second stream, so that its transfer
+    // overlaps the Cholesky factorisation; the solve waits for it just
+    // before its first read
+    if (!h->cp) {
+      GS_CUDA(cudaStreamCreateWithFlags(&h->cp, cudaStreamNonBlocking));
+      GS_CUDA(cudaEventCreateWithFlags(&h->cp_ev, cudaEventDisableTiming));
+    }
+    const bool a_first = h->opts.inverse == 1 && which == GSYEIG_SMALLEST;
+    double *d1 = a_first ? dA : dB, *d2 = a_first ? dB : dA;
+    const double *s1 = a_first ? A : B, *s2 = a_first ? B : A;
+    const int64_t l1 = a_first ? lda : ldb, l2 = a_first ? ldb : lda;
+    GS_CUDA(cudaMemcpy2DAsync(d1, n * sizeof(double), s1, l1 * sizeof(double), n * sizeof(double), n,
                               cudaMemcpyHostToDevice, st));
-    GS_CUDA(cudaMemcpy2DAsync(dB, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), n,
-                              cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaStreamWaitEvent(h->cp, h->ev[0], 0));  // the staging buffer is free once the call has begun
+    GS_CUDA(cudaMemcpy2DAsync(d2, n * sizeof(double), s2, l2 * sizeof(double), n * sizeof(double), n,
+                              cudaMemcpyHostToDevice, h->cp));
+    GS_CUDA(cudaEventRecord(h->cp_ev, h->cp));
+    copy_pending.st = h->cp;
   }
+  // the second matrix has landed (no-op for device inputs)
+  auto second_ready = [&]() -> int {
+    if (hostA) GS_CUDA(cudaStreamWaitEvent(st, h->cp_ev, 0));
+    return GSYEIG_SUCCESS;
+  };
   if (!hostA && h->opts.preserve_inputs == 1) {  // solve on copies; the caller's A, B stay as they were
     GS_TRY(h->pA.ensure((size_t)n * n * sizeof(double)));
     GS_TRY(h->pB.ensure((size_t)n * n * sizeof(double)));
@@ -1261,6 +1415,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   }
   const bool verify = h->opts.verify == 1;
   if (verify) {  // the originals, completed from the triangles the route reads (A lower, B upper)
+    GS_TRY(second_ready());
     GS_TRY(h->vA.ensure((size_t)n * n * sizeof(double)));
     GS_TRY(h->vB.ensure((size_t)n * n * sizeof(double)));
     GS_CUDA(cudaMemcpy2DAsync(h->vA.p, n * sizeof(double), dA, dlda * sizeof(double), n * sizeof(double), n,
@@ -1295,6 +1450,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     GS_CUDA(cudaMemcpyAsync(&flag, fw.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
     GS_TRY(gemm_check(h));  // an expired GEMM wait, not a pivot, may have set the flag
+    GS_TRY(second_ready());
     if (flag) {  // A indefinite: put its diagonal back, take the direct route
       GS_CUDA(cudaMemcpy2DAsync(dA, (size_t)(dlda + 1) * sizeof(double), h->diag.p, sizeof(double), sizeof(double), n,
                                 cudaMemcpyDeviceToDevice, st));
@@ -1321,9 +1477,10 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     if (info) info->potrf_index = flag;
     return GSYEIG_NOT_SPD;
   }
+  GS_TRY(second_ready());
   const bool ki = h->opts.implicit == 1;
   if (ki && h->opts.fp64_symv == 1) return GSYEIG_NOT_SUPPORTED;  // KI runs on the double-float tiles
-  if (ki && h->opts.mixed == 1) return GSYEIG_NOT_SUPPORTED;
+  if (ki && (h->opts.mixed != 0 || h->opts.block_start == 1)) return GSYEIG_NOT_SUPPORTED;
   if (!ki) {
     // gs2: C = U^-T G U^-1 over G (diagonal-block inverses reused from gs1)
     GS_TRY(sygst_blocked(st, n, dG, dldg, dF, dldf, nb, fw, true));
@@ -1343,9 +1500,58 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   double ms_ke3 = 0, theta_min = 1.0;
   int status;
   if (h->opts.mixed == 1) {
-    // fp32 block Lanczos + FP64 block refinement; B's definiteness is not
-    // checked here on the inverse route
-    status = lanczos_mixed(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3);
+    // fp32 block Lanczos, then the FP64-accurate Lanczos started from the sum
+    // of the s wanted fp32 Ritz vectors, with Ritz tests every check_every
+    // (default 16) steps: the start vector lies in the wanted invariant
+    // subspace up to the fp32 stage's error, so the FP64 stage stops early
+    const double *blk = nullptr;
+    status = lanczos_mixed(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
+                           nullptr, 0, &blk);
+    if (status != GSYEIG_SUCCESS && status != GSYEIG_NOT_SUPPORTED) return status;
+    gsyeig_info keep{};
+    if (info) keep = *info;
+    const gsyeig_opts saved = h->opts;
+    if (status == GSYEIG_SUCCESS) {
+      GS_TRY(h->mx_ones.ensure((size_t)s * sizeof(double)));
+      const std::vector<double> ones((size_t)s, 1.0);
+      GS_CUDA(cudaMemcpyAsync(h->mx_ones.p, ones.data(), (size_t)s * sizeof(double), cudaMemcpyHostToDevice, st));
+      h->opts.start_block = blk;
+      h->opts.start_cols = s;
+      h->opts.ld_start = n;
+      h->opts.start_weights = h->mx_ones.d();
+      h->opts.filter_degree = 0;
+      if (h->opts.check_every == 0) h->opts.check_every = 16;
+    }
+    status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
+                         nullptr, inv ? &theta_min : nullptr, nullptr, 0);
+    h->opts = saved;
+    if (info) {  // ms_refine (the FP64 stage) is set with the stage times below
+      info->block_steps = keep.block_steps;
+      info->ms_block_lanczos = keep.ms_block_lanczos;
+      info->matvecs += keep.matvecs;
+    }
+  } else if (h->opts.mixed == 2 || (h->opts.block_start == 1 && h->opts.start_block)) {
+    // fp32 block Lanczos (or the caller's block) + FP64 block refinement;
+    // B's definiteness is not checked here on the inverse route
+    status = lanczos_mixed(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
+                           dF, dldf);
+    if (status == GSYEIG_NO_CONVERGENCE || status == GSYEIG_NOT_SUPPORTED) {
+      // the block refinement did not reach the tolerance (small relative
+      // gaps at the wanted end, e.g. the smallest eigenvalues on the direct
+      // route): the FP64-accurate Lanczos stage takes over
+      gsyeig_info keep{};
+      if (info) keep = *info;
+      status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
+                           nullptr, inv ? &theta_min : nullptr, dF, dldf);
+      if (info) {
+        info->refine_fallback = 1;
+        info->block_steps = keep.block_steps;
+        info->refine_iters = keep.refine_iters;
+        info->ms_block_lanczos = keep.ms_block_lanczos;
+        info->ms_refine = keep.ms_refine;
+        info->matvecs += keep.matvecs;
+      }
+    }
   } else {
     status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
                          ki ? h->kinv.d() : nullptr, inv ? &theta_min : nullptr, dF, dldf);
@@ -1354,6 +1560,16 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   if (inv && !(theta_min > 0.0)) {
     if (info) info->inverse = 1;
     return GSYEIG_NOT_SPD;
+  }
+  if (inv && !ki) {  // (variant KI holds the untransformed matrix, not C')
+    // needed when the wanted mu span a wide range (a lambda near zero): the
+    // defect of X^T B X grows like mu_max / mu_min times the rounding level
+    double mu_lo = 0.0, mu_hi = 0.0;  // the wanted mu, ascending: all must be positive
+    GS_CUDA(cudaMemcpyAsync(&mu_lo, h->hw.d(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaMemcpyAsync(&mu_hi, h->hw.d() + (s - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaStreamSynchronize(st));
+    if (mu_lo > 0.0 && theta_min > 0.0 && mu_hi > 1e3 * mu_lo)
+      GS_TRY(b_orthonormalise_inverse(h, st, n, s, dG, dldg, dX, dldx, h->hw.d()));
   }
   GS_CUDA(cudaEventRecord(h->ev[4], st));
   // bt1: X = U^-1 Y
@@ -1391,6 +1607,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     const double ke = elapsed(h->ev[3], h->ev[4]);
     info->ms_ke3 = ms_ke3;
     info->ms_ke = ke - ms_ke3;
+    if (h->opts.mixed == 1) info->ms_refine = ke - info->ms_block_lanczos;  // the FP64 Lanczos stage
     info->ms_bt1 = elapsed(h->ev[4], h->ev[8]);
     info->ms_total = elapsed(h->ev[0], h->ev[8]);
     info->kernel_launches = g_launches.load() - l0;

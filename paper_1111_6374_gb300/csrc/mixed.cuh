@@ -46,6 +46,10 @@ int inf_norm(cudaStream_t st, int64_t m, const double *T, int64_t ldt, double *o
 // out[c] = X(:, c) . Y(:, c) for c < cols
 int column_dots(cudaStream_t st, int64_t n, int64_t cols, const double *X, int64_t ldx, const double *Y, int64_t ldy,
                 double *out);
+// M(i, j) *= theta_i^pa theta_j^pb (m x m; theta device, positive)
+int scale_by_powers(cudaStream_t st, int64_t m, double *M, int64_t ldm, const double *theta, double pa, double pb);
+// out[0] (device double) = the 1-norm of the n x n M
+int mat_norm1(cudaStream_t st, int64_t n, const double *M, int64_t ldm, double *out);
 // dst(:, c) = src(:, idx[c]) for c < cnt (idx device)
 int gather_cols(cudaStream_t st, int64_t n, int64_t cnt, const int *idx, const double *src, int64_t lds, double *dst,
                 int64_t ldd);

@@ -232,6 +232,80 @@ __global__ void k_mlp_init(int nin, int H, int nout, uint64_t seed, float *__res
   }
 }
 
+// Alignment of two sets of eigenvectors through their overlaps P (s x s,
+// P[j, i] = x_j^T B y_i): out_j = sgn_j y_{pi_j} - x_j with pi_j the best
+// match of x_j among the y and sgn_j the sign of that overlap; columns whose
+// best |overlap| is below 1/2 (a crossing) get out_j = 0.  match[j] (may be
+// NULL) = the best |overlap|.
+__global__ void k_ws_align(int64_t n, int s, const double *__restrict__ X, int64_t ldx, const double *__restrict__ Y,
+                           int64_t ldy, const double *__restrict__ P, int64_t ldp, double *__restrict__ out,
+                           int64_t ldo, float *__restrict__ match) {
+  const int j = blockIdx.y;
+  __shared__ int pi;
+  __shared__ double sg;
+  if (threadIdx.x == 0) {
+    int bi = 0;
+    double bv = -1.0;
+    for (int i = 0; i < s; i++) {
+      const double v = fabs(P[j + (int64_t)i * ldp]);
+      if (v > bv) {
+        bv = v;
+        bi = i;
+      }
+    }
+    pi = bi;
+    sg = (bv >= 0.5) ? (P[j + (int64_t)bi * ldp] >= 0.0 ? 1.0 : -1.0) : 0.0;
+    if (match && blockIdx.x == 0) match[j] = (float)bv;
+  }
+  __syncthreads();
+  const double *y = Y + (int64_t)pi * ldy, *x = X + (int64_t)j * ldx;
+  double *o = out + (int64_t)j * ldo;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = (sg != 0.0) ? sg * y[i] - x[i] : 0.0;
+}
+
+// targets t_j = clamp(-(D_j . BE_j) / (D_j . BD_j), lo, hi) (0 where D_j = 0)
+__global__ void k_ws_coef(int64_t n, int s, const double *__restrict__ D, int64_t ldd, const double *__restrict__ BD,
+                          int64_t ldbd, const double *__restrict__ BE, int64_t ldbe, double lo, double hi,
+                          float *__restrict__ t) {
+  __shared__ double r1[32], r2[32];
+  const int j = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = D[i + (int64_t)j * ldd];
+    a = fma(d, BE[i + (int64_t)j * ldbe], a);
+    b = fma(d, BD[i + (int64_t)j * ldbd], b);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = a;
+    r2[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double num = 0.0, den = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+      num += r1[k];
+      den += r2[k];
+    }
+    t[j] = (den > 0.0) ? (float)fmin(hi, fmax(lo, -num / den)) : 0.f;
+  }
+}
+
+// out_j = X_j - clamp(c_j, lo, hi) D_j (the extrapolated start block)
+__global__ void k_ws_extrapolate(int64_t n, int s, const double *__restrict__ X, int64_t ldx,
+                                 const double *__restrict__ D, int64_t ldd, const float *__restrict__ c, double lo,
+                                 double hi, double *__restrict__ out, int64_t ldo) {
+  const int j = blockIdx.y;
+  const double cj = fmin(hi, fmax(lo, (double)c[j]));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i + (int64_t)j * ldo] = X[i + (int64_t)j * ldx] - cj * D[i + (int64_t)j * ldd];
+}
+
 // Features of the problem at step t for the next one: with g the mean
 // spacing of theta(t) (s ascending Ritz values), f_j = (theta_j(t) -
 // theta_s(t)) / g, f_{s+j} = (theta_j(t) - theta_j(t-1)) / g, f_{2s} =
@@ -251,27 +325,6 @@ __global__ void k_ws_features(int s, const double *__restrict__ th, const double
   }
 }
 
-// Targets for the step-t features from the solution at t+1: o_0 =
-// (theta_s(t+1) - theta_s(t)) / g, o_j = ||P[:, j]|| for the overlaps
-// P = X(t+1)^T B X(t) (s x s, ld ldp): the cosine between previous
-// eigenvector j and the next wanted subspace.
-__global__ void k_ws_targets(int s, const double *__restrict__ th_next, const double *__restrict__ scal,
-                             const double *__restrict__ P, int64_t ldp, float *__restrict__ o) {
-  for (int j = threadIdx.x; j < s; j += blockDim.x) {
-    double a = 0.0;
-    for (int i = 0; i < s; i++) a = fma(P[i + (int64_t)j * ldp], P[i + (int64_t)j * ldp], a);
-    o[1 + j] = (float)fmin(1.0, sqrt(a));
-  }
-  if (threadIdx.x == 0) o[0] = (float)((th_next[s - 1] - scal[0]) / scal[1]);
-}
-
-// Network output to a start block and a filter cut: weights w_j =
-// clamp(o_j, wmin, 1), cut = theta_s(t) + g (o_0 + margin).
-__global__ void k_ws_decode(int s, const float *__restrict__ o, const double *__restrict__ scal, double margin,
-                            double wmin, double *__restrict__ w, double *__restrict__ cut) {
-  for (int j = threadIdx.x; j < s; j += blockDim.x) w[j] = fmin(1.0, fmax(wmin, (double)o[1 + j]));
-  if (threadIdx.x == 0) *cut = scal[0] + scal[1] * ((double)o[0] + margin);
-}
 
 
 int mlp_gemm(cudaStream_t st, int M, int N, int K, const float *A, int64_t sam, int64_t sak, const float *B,
@@ -457,30 +510,46 @@ int gsyeig_ws_features(int64_t s, const double *theta, const double *theta_prev,
   return GSYEIG_SUCCESS;
 }
 
-int gsyeig_ws_targets(int64_t s, const double *theta_next, const double *scal, const double *P, int64_t ldp,
-                      float *targets, void *stream) {
-  if (s < 1 || s > 4096) return -1;
-  if (!theta_next) return -2;
-  if (!scal) return -3;
-  if (!P) return -4;
-  if (ldp < s) return -5;
-  if (!targets) return -6;
+int gsyeig_ws_align(int64_t n, int64_t s, const double *X, int64_t ldx, const double *Y, int64_t ldy, const double *P,
+                    int64_t ldp, double *out, int64_t ldo, float *match, void *stream) {
+  if (n < 1) return -1;
+  if (s < 1 || s > 4096) return -2;
+  if (!X || ldx < n) return -3;
+  if (!Y || ldy < n) return -5;
+  if (!P || ldp < s) return -7;
+  if (!out || ldo < n) return -9;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_ws_targets<<<1, 256, 0, st>>>((int)s, theta_next, scal, P, ldp, targets);
+  k_ws_align<<<dim3((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)s), 256, 0, st>>>(
+      n, (int)s, X, ldx, Y, ldy, P, ldp, out, ldo, match);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
 }
 
-int gsyeig_ws_decode(int64_t s, const float *outputs, const double *scal, double margin, double wmin, double *weights,
-                     double *cut, void *stream) {
-  if (s < 1 || s > 4096) return -1;
-  if (!outputs) return -2;
-  if (!scal) return -3;
-  if (!weights) return -6;
-  if (!cut) return -7;
+int gsyeig_ws_coef_targets(int64_t n, int64_t s, const double *D, int64_t ldd, const double *BD, int64_t ldbd,
+                           const double *BE, int64_t ldbe, double lo, double hi, float *targets, void *stream) {
+  if (n < 1) return -1;
+  if (s < 1 || s > 4096) return -2;
+  if (!D || !BD || !BE) return -3;
+  if (!targets) return -11;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_ws_decode<<<1, 256, 0, st>>>((int)s, outputs, scal, margin, wmin, weights, cut);
+  k_ws_coef<<<(unsigned)s, 256, 0, st>>>(n, (int)s, D, ldd, BD, ldbd, BE, ldbe, lo, hi, targets);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int gsyeig_ws_extrapolate(int64_t n, int64_t s, const double *X, int64_t ldx, const double *D, int64_t ldd,
+                          const float *coef, double lo, double hi, double *out, int64_t ldo, void *stream) {
+  if (n < 1) return -1;
+  if (s < 1 || s > 4096) return -2;
+  if (!X || ldx < n) return -3;
+  if (!D || ldd < n) return -5;
+  if (!coef) return -7;
+  if (!out || ldo < n) return -10;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_ws_extrapolate<<<dim3((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)s), 256, 0, st>>>(
+      n, (int)s, X, ldx, D, ldd, coef, lo, hi, out, ldo);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;

@@ -43,7 +43,7 @@ __device__ __forceinline__ double opx(const double *X, int64_t ld, bool kcontig,
 // bf16 elements) or UMMA core-matrix tiles (tcgen05 engine, row blocks of rb).
 struct DigitLayout {
   bool umma;
-  int rb;  // UMMA row block (128 for A, 64 for B)
+  int rb;  // UMMA row block (128 for A, 32 for B)
 };
 
 __device__ __forceinline__ size_t digit_off(const DigitLayout &L, int p, int64_t r, int64_t k, int64_t Rpad,

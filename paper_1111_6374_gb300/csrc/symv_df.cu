@@ -14,10 +14,14 @@
 // used twice (C_ij w_j and C_ij^T w_i): the kernel is HBM-bound.
 //
 // Layout: tile t = bi (bi + 1) / 2 + bj for bi >= bj; within a tile,
-// element (r, c) at (r ^ (c & 31)) + 64 c (column-major with the row index
-// XOR-swizzled by the column, so that a warp reading 32 rows of one column
-// and a warp reading one row of 32 columns both touch 32 distinct shared
-// memory banks); hi and lo in two arrays.
+// element (r, c) at (r ^ 2 (c & 15)) + 64 c (column-major, the row index
+// XOR-swizzled by an even amount that depends on the column: rows 2m and
+// 2m + 1 stay adjacent, so a thread reads a pair of rows with one 64-bit
+// load, and both a warp reading 64 rows of one column and a warp reading
+// one row pair of 32 columns are free of bank conflicts); hi and lo in two
+// arrays.
+// The arithmetic runs on packed pairs (fma/mul/add.rn.f32x2): a thread
+// carries two compensated accumulators, one per row of its pair.
 // C is stored scaled by the power of two 2^-e that brings max|C| into
 // [1/2, 1), so that neither fp32 half overflows or underflows for pencils
 // of any scale; the row sums are scaled back by 2^e.
@@ -32,12 +36,7 @@ namespace gs {
 namespace {
 
 constexpr int TS = 64;           // tile size
-constexpr int DF_THREADS = 256;  // 8 warps: rows lane + 32 (warp & 1), column group warp >> 1
-
-__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-  p = a * b;
-  e = fmaf(a, b, -p);
-}
+constexpr int DF_THREADS = 256;  // 8 warps: row pairs x column groups of 8 (row sums); columns x row groups of 16
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
@@ -45,12 +44,50 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// (s, c) += (p, e): compensated accumulation of a product given as p + e
-__device__ __forceinline__ void acc2(float &s, float &c, float p, float e) {
-  float t, q;
-  two_sum(s, p, t, q);
+// packed pairs of fp32 (low half: first element) and their arithmetic
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pmul(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 padd(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 psub(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 pfma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float2 unpack(f32x2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+// One compensated step on both lanes: (s, c) += (c_hi + c_lo)(x_hi + x_lo)
+// with p = c_hi x_hi, its exact error from an FMA, the cross terms
+// c_hi x_lo + c_lo x_hi in plain fp32, and the two-sum error of s + p
+// (Ogita, Rump, Oishi 2005).  The negated x halves come precomputed, so
+// en = p - c_hi x_hi - c_hi x_lo - c_lo x_hi is the negated low-order part.
+__device__ __forceinline__ void dot2_step(f32x2 &s, f32x2 &c, f32x2 ch, f32x2 cl, f32x2 xh, f32x2 nxh, f32x2 nxl) {
+  const f32x2 p = pmul(ch, xh);
+  f32x2 en = pfma(ch, nxh, p);
+  en = pfma(ch, nxl, en);
+  en = pfma(cl, nxh, en);
+  const f32x2 t = padd(s, p);
+  const f32x2 bb = psub(t, s);
+  const f32x2 q = padd(psub(s, psub(t, bb)), psub(p, bb));
+  c = psub(padd(c, q), en);
   s = t;
-  c += q + e;
 }
 
 // Largest |entry| of the stored part of M (as its bit pattern: for
@@ -104,7 +141,7 @@ __global__ void k_op_build(int64_t n, int64_t NT, const double *__restrict__ C, 
     double v = 0.0;
     if (i < n && j < n && !(tri && j > i)) v = ldexp(trans ? C[j + i * ldc] : C[i + j * ldc], -e);
     const float vh = (float)v;
-    const int pos = (r ^ (c & 31)) + TS * c;
+    const int pos = (r ^ (2 * (c & 15))) + TS * c;
     h[pos] = vh;
     l[pos] = (float)(v - (double)vh);
   }
@@ -182,18 +219,20 @@ constexpr int TILE_BYTES = TS * TS * 4;  // one of hi / lo
 // mode DF_SYM: z = M w for the symmetric M whose lower triangle is stored
 // (row sums of every tile, column sums of the off-diagonal ones);
 // DF_ROWS: z = L w and DF_COLS: z = L^T w for the lower-triangular L stored.
-__global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, const float *__restrict__ hi,
+__global__ void __launch_bounds__(DF_THREADS, CTAS_PER_SM) k_symv_df(int NT, int64_t npad, const float *__restrict__ hi,
                                                         const float *__restrict__ lo, const float2 *__restrict__ ws,
                                                         float2 *__restrict__ W, int *err, int mode, uint32_t spin) {
   extern __shared__ __align__(128) unsigned char smem[];
   float *sh = reinterpret_cast<float *>(smem);                       // NSTAGE x (hi tile, lo tile)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)NSTAGE * 2 * TILE_BYTES);
-  __shared__ float2 xr[TS], xc[TS];  // w of the tile's column block (row sums), row block (col sums)
-  __shared__ float2 rowp[4][TS];     // row-sum partials of the 4 column groups
-  __shared__ float2 colp[4][TS];     // column-sum partials of the 4 row groups
+  // w of the tile's column block for the row sums, as duplicated pairs (x_hi, x_hi), (-x_hi, -x_hi),
+  // (-x_lo, -x_lo); w of its row block for the column sums, as arrays read in row pairs
+  __shared__ f32x2 xrh[TS], xrnh[TS], xrnl[TS];
+  __shared__ __align__(8) float xch[TS], xcnh[TS], xcnl[TS];
+  __shared__ float2 rowp[8][TS];  // row-sum partials of the 8 column groups
+  __shared__ float2 colp[4][TS];  // column-sum partials of the 4 row groups
   __shared__ int s_fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = lane + 32 * (warp & 1), g = warp >> 1;  // row, column group (16 columns)
   const int ntiles = NT * (NT + 1) / 2;
   const int mine = (blockIdx.x < (unsigned)ntiles) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   if (threadIdx.x == 0) {
@@ -225,56 +264,55 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
     const bool diag = (bi == bj);
     const bool do_rows = mode != DF_COLS;                          // block-uniform
     const bool do_cols = (mode == DF_SYM && !diag) || mode == DF_COLS;
-    if (threadIdx.x < TS) xr[threadIdx.x] = ws[(int64_t)bj * TS + threadIdx.x];
-    else if (threadIdx.x < 2 * TS) xc[threadIdx.x - TS] = ws[(int64_t)bi * TS + threadIdx.x - TS];
+    if (threadIdx.x < TS) {
+      const float2 v = ws[(int64_t)bj * TS + threadIdx.x];
+      const int q = threadIdx.x;
+      asm("mov.b64 %0, {%1, %1};" : "=l"(xrh[q]) : "f"(v.x));
+      asm("mov.b64 %0, {%1, %1};" : "=l"(xrnh[q]) : "f"(-v.x));
+      asm("mov.b64 %0, {%1, %1};" : "=l"(xrnl[q]) : "f"(-v.y));
+    } else if (threadIdx.x < 2 * TS) {
+      const int q = threadIdx.x - TS;
+      const float2 v = ws[(int64_t)bi * TS + q];
+      xch[q] = v.x;
+      xcnh[q] = -v.x;
+      xcnl[q] = -v.y;
+    }
     const int b = i % NSTAGE;
     const bool ok = mbar_wait(&full[b], (uint32_t)((i / NSTAGE) & 1), spin);
     if (!ok) s_fail = 1;
     __syncthreads();
     if (s_fail) break;
-    const float *h = sh + (size_t)(b * 2) * TS * TS, *l = h + TS * TS;
-    float ch[16], cl[16];
+    const f32x2 *h2 = reinterpret_cast<const f32x2 *>(sh + (size_t)(b * 2) * TS * TS);
+    const f32x2 *l2 = h2 + TS * TS / 2;
     if (do_rows) {
-      // row sums: thread (row r, column group g) over columns 16 g .. 16 g + 15
+      // row sums: thread (rows 2 lane, 2 lane + 1) over the 8 columns of its
+      // warp; (c & 15) = 8 (warp & 1) + k, so the swizzle is rb ^ 2k
+      const int rb = (2 * lane) ^ (16 * (warp & 1));
+      f32x2 sr = 0ull, cr = 0ull;
 #pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const int col = g * 16 + k, pos = (r ^ (col & 31)) + TS * col;
-        ch[k] = h[pos];
-        cl[k] = l[pos];
+      for (int k = 0; k < 8; k++) {
+        const int col = 8 * warp + k;
+        const int pos = (rb ^ (2 * k)) + TS * col;
+        dot2_step(sr, cr, h2[pos >> 1], l2[pos >> 1], xrh[col], xrnh[col], xrnl[col]);
       }
-      float rs = 0.f, rc = 0.f;
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const float2 x = xr[g * 16 + k];
-        float p, e;
-        two_prod(ch[k], x.x, p, e);
-        e = fmaf(ch[k], x.y, e);
-        e = fmaf(cl[k], x.x, e);
-        acc2(rs, rc, p, e);
-      }
-      rowp[g][r] = make_float2(rs, rc);
+      const float2 a = unpack(sr), c = unpack(cr);
+      *reinterpret_cast<float4 *>(&rowp[warp][2 * lane]) = make_float4(a.x, c.x, a.y, c.y);
     }
     if (do_cols) {
-      // column sums (C_ij^T w_i): thread (column c = r, row group g) over
-      // rows 16 g .. 16 g + 15, read across the swizzle without conflicts
-      const int c = r;
+      // column sums (C_ij^T w_i): thread (column cc, row group g) over the
+      // 8 row pairs 16 g + 2k, 16 g + 2k + 1, one accumulator per row parity
+      const int cc = lane + 32 * (warp & 1), g = warp >> 1;
+      const int cb = (16 * g) ^ (2 * (cc & 15));
+      f32x2 sc = 0ull, ccp = 0ull;
 #pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const int row = g * 16 + k, pos = (row ^ (c & 31)) + TS * c;
-        ch[k] = h[pos];
-        cl[k] = l[pos];
+      for (int k = 0; k < 8; k++) {
+        const int row = 16 * g + 2 * k;
+        const int pos = (cb ^ (2 * k)) + TS * cc;
+        dot2_step(sc, ccp, h2[pos >> 1], l2[pos >> 1], *reinterpret_cast<const f32x2 *>(&xch[row]),
+                  *reinterpret_cast<const f32x2 *>(&xcnh[row]), *reinterpret_cast<const f32x2 *>(&xcnl[row]));
       }
-      float cs = 0.f, cc = 0.f;
-#pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const float2 x = xc[g * 16 + k];
-        float p, e;
-        two_prod(ch[k], x.x, p, e);
-        e = fmaf(ch[k], x.y, e);
-        e = fmaf(cl[k], x.x, e);
-        acc2(cs, cc, p, e);
-      }
-      colp[g][c] = make_float2(cs, cc);
+      const float2 a = unpack(sc), c = unpack(ccp);
+      colp[g][cc] = df_add(make_float2(a.x, c.x), make_float2(a.y, c.y));
     }
     __syncthreads();  // stage b fully read; partials complete
     if (threadIdx.x == 0 && issued < mine) {
@@ -284,7 +322,8 @@ __global__ void __launch_bounds__(DF_THREADS) k_symv_df(int NT, int64_t npad, co
     if (do_rows && threadIdx.x < TS) {
       // rows of block bi: combine the 4 column groups
       const int rr = threadIdx.x;
-      float2 a = df_add(df_add(rowp[0][rr], rowp[1][rr]), df_add(rowp[2][rr], rowp[3][rr]));
+      const float2 a = df_add(df_add(df_add(rowp[0][rr], rowp[1][rr]), df_add(rowp[2][rr], rowp[3][rr])),
+                              df_add(df_add(rowp[4][rr], rowp[5][rr]), df_add(rowp[6][rr], rowp[7][rr])));
       W[(int64_t)bj * npad + (int64_t)bi * TS + rr] = a;
     } else if (do_cols && threadIdx.x >= TS && threadIdx.x < 2 * TS) {
       const int cc = threadIdx.x - TS;

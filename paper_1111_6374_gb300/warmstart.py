@@ -1,20 +1,21 @@
 """Learned warm start for sequences of related problems (binding and driver).
 
-The paper's Section 3 motivates sequences of related eigenproblems (each
-self-consistency cycle of a DFT code solves dozens).  Here a small MLP,
-trained on the GPU by the library's own forward and backward kernels
-(``gsyeig_mlp_*``: bf16 tcgen05 products, fp32 parameters and Adam), reads
-a solved problem's Ritz values and the parameter step and proposes, for the
-next problem, the weights of a start block built from the previous
-eigenvectors and the cut of a Chebyshev filter applied to it
-(``gsyeig_opts.start_block / start_weights / filter_*``).  The solver's
-residual test alone decides acceptance; a random start is the fallback
-when a proposal does not converge.
+Section 3 of the paper motivates sequences of related eigenproblems (each
+self-consistency cycle of a DFT code solves dozens).  Here a small MLP
+(two hidden layers of 256), trained on the GPU by the library's own forward
+and backward kernels (``gsyeig_mlp_*``: bf16 tcgen05 products, fp32
+parameters and Adam), reads the previous two problems' eigenvalues and the
+overlaps of their eigenvectors and predicts, per wanted pair, how far to
+extrapolate each eigenvector along the sequence.  The extrapolated block is
+the start block of the solver's FP64 block refinement
+(``gsyeig_opts.block_start``).  The solver's residual test alone decides
+acceptance; a start block whose refinement does not converge falls back to
+the FP64 Lanczos stage inside the library.
 
-This module only sequences library calls: features, targets and the
-decoding of the network's outputs run in the library's kernels
-(``gsyeig_ws_features / _targets / _decode``), and torch supplies device
-memory.
+This module only sequences library calls: features, alignment, training
+targets and the extrapolation run in the library's kernels
+(``gsyeig_ws_features / _align / _coef_targets / _extrapolate``), and torch
+supplies device memory.
 """
 from __future__ import annotations
 
@@ -93,84 +94,161 @@ class Mlp:
 
 
 class SequenceSolver:
-    """Solves a sequence of pencils (A_k, B) for the s smallest eigenpairs,
-    starting each solve from the previous solution in one of three ways:
+    """Solves a sequence of pencils (A_t, B) for the s smallest eigenpairs,
+    each solve started from the previous solutions in one of three ways:
 
-    * ``"random"``: the counter-based random start (no reuse);
-    * ``"reuse"``: the start vector U (sum_j x_j) from the previous
-      eigenvectors, no filter (the unlearned control);
-    * ``"learned"``: weights and a filter cut proposed by the network from
-      the previous two problems' Ritz values.
+    * ``"random"``: the counter-based random start vector of the plain solver;
+    * ``"reuse"``: the start vector F sum_j x_j(t-1) built from the previous
+      problem's eigenvectors, unchanged (the unlearned control);
+    * ``"learned"``: the same construction from the block the network
+      proposes: every previous eigenvector extrapolated along the sequence,
+      x_j(t-1) + c_j (x_j(t-1) - x_j(t-2)) (aligned by their overlaps), with
+      the coefficients c_j predicted from the previous two problems'
+      eigenvalues and overlaps.
 
-    Every method tests convergence every ``check_every`` steps."""
+    Every method runs the same Lanczos iteration with Ritz tests every
+    ``check_every`` steps, so a start vector rich in the wanted eigenvectors
+    stops early.  The solver's residual test decides acceptance in every
+    case."""
 
-    def __init__(self, s: int, method: str, mlp: Mlp | None = None, check_every: int = 16, filter_degree: int = 8,
-                 margin: float = 2.0, wmin: float = 0.05, dt_rel: float = 1.0, device=0, **opts):
+    C_LO, C_HI = 0.0, 1.5  # range of the extrapolation coefficients
+
+    def __init__(self, s: int, method: str, B: torch.Tensor, mlp: Mlp | None = None, device=0, check_every: int = 16,
+                 **opts):
         assert method in ("random", "reuse", "learned")
-        self.s, self.method, self.mlp = s, method, mlp
-        self.check_every, self.degree, self.margin, self.wmin, self.dt_rel = (check_every, filter_degree, margin,
-                                                                              wmin, dt_rel)
-        self.solver = Solver(device, check_every=check_every, **opts)
+        self.s, self.method, self.mlp, self.B = s, method, mlp, B
+        # the inverse route (largest mu = 1/lambda of L^-T B L^-1) by default;
+        # a pencil whose A is not definite falls back to the direct route
+        # inside the library
+        self.solver = Solver(device, **{"inverse": 1, "check_every": check_every, **opts})
         self.lib = self.solver.lib
-        self.prev = []  # (w, X, info) of the last two solves
+        self.prev = []  # (w, X) of the last two solves
         dev = torch.device("cuda", device)
         self.dev = dev
-        self.feat = torch.empty(2 * s + 1, device=dev, dtype=torch.float32)
-        self.scal = torch.empty(2, device=dev, dtype=torch.float64)
-        self.weights = torch.empty(s, device=dev, dtype=torch.float64)
-        self.cut = torch.empty(1, device=dev, dtype=torch.float64)
+        n = B.shape[0]
+        self.D = colmajor_empty(n, s, device=dev)
+        self.start = colmajor_empty(n, s, device=dev)
+        self.weights = torch.ones(s, device=dev, dtype=torch.float64)
 
-    def features(self, w, w_prev, out=None, scal=None):
-        out = self.feat if out is None else out
-        scal = self.scal if scal is None else scal
-        st = self.lib.gsyeig_ws_features(self.s, _p(w), _p(w_prev), self.dt_rel, _p(out), _p(scal), _stream(self.dev))
+    def _st(self):
+        return _stream(self.dev)
+
+    def overlaps(self, X, Y):
+        """P = X^T B Y (s x s) on the library's GEMM engine (B symmetric: its
+        transpose is the same matrix, in column-major storage)."""
+        return self.solver.gemm(X, self.solver.gemm(self.B.t(), Y), transA=True)
+
+    def align(self, X, Y, out, match=None):
+        """out_j = sgn_j Y[:, pi_j] - X[:, j] (gsyeig_ws_align)."""
+        P = self.overlaps(X, Y)
+        n, s = X.shape
+        st = self.lib.gsyeig_ws_align(n, s, _p(X), X.stride(1), _p(Y), Y.stride(1), _p(P), P.stride(1), _p(out),
+                                      out.stride(1), _p(match), self._st())
+        if st != 0:
+            raise GsyeigError(st, "ws_align")
+        return out
+
+    def features(self, w, w_prev, X, X_prev):
+        """Network input for the problem after (w, X): the eigenvalue features
+        of gsyeig_ws_features (2s + 1) and the best overlaps of the eigenvectors
+        with the previous ones (s); also leaves the aligned difference in self.D."""
+        s = self.s
+        f = torch.empty(3 * s + 1, device=self.dev, dtype=torch.float32)
+        scal = torch.empty(2, device=self.dev, dtype=torch.float64)
+        st = self.lib.gsyeig_ws_features(s, _p(w), _p(w_prev), 1.0, _p(f), _p(scal), self._st())
         if st != 0:
             raise GsyeigError(st, "ws_features")
-        return out, scal
+        self.align(X, X_prev, self.D, match=f[2 * s + 1:])
+        return f
+
+    def targets(self, X_prev, X, X_next, out):
+        """B-optimal extrapolation coefficients of x_j(t) (gsyeig_ws_coef_targets)."""
+        n, s = X.shape
+        D = self.align(X, X_prev, colmajor_empty(n, s, device=self.dev))
+        E = self.align(X, X_next, colmajor_empty(n, s, device=self.dev))
+        BD = self.solver.gemm(self.B.t(), D)
+        BE = self.solver.gemm(self.B.t(), E)
+        st = self.lib.gsyeig_ws_coef_targets(n, s, _p(D), D.stride(1), _p(BD), BD.stride(1), _p(BE), BE.stride(1),
+                                             self.C_LO, self.C_HI, _p(out), self._st())
+        if st != 0:
+            raise GsyeigError(st, "ws_coef_targets")
+        return out
 
     def solve(self, A: torch.Tensor, B: torch.Tensor):
-        """One solve of the sequence (A and B are not modified).  Returns
-        (w, X, info, ms); info["fallback"] is 1 when a proposal did not
-        converge and the random start took over."""
+        """One solve of the sequence (A, B not modified): (w, X, info, ms)."""
         s, sol = self.s, self.solver
-        opts = dict(start_block=None, start_weights=None, filter_degree=0, filter_cut=0.0, filter_edge=0.0)
+        opts = dict(start_block=None, start_weights=None)
         if self.method != "random" and self.prev:
-            opts["start_block"] = self.prev[-1][1]
+            opts.update(start_block=self.prev[-1][1], start_weights=self.weights)
         if self.method == "learned" and len(self.prev) >= 2:
-            feat, scal = self.features(self.prev[-1][0], self.prev[-2][0])
-            out = self.mlp.forward(feat.unsqueeze(0))
-            st = self.lib.gsyeig_ws_decode(s, _p(out), _p(scal), self.margin, self.wmin, _p(self.weights),
-                                           _p(self.cut), _stream(self.dev))
+            (w1, X1), (w0, X0) = self.prev[-1], self.prev[-2]
+            f = self.features(w1, w0, X1, X0)
+            c = self.mlp.forward(f.unsqueeze(0))
+            n = X1.shape[0]
+            st = self.lib.gsyeig_ws_extrapolate(n, s, _p(X1), X1.stride(1), _p(self.D), self.D.stride(1), _p(c),
+                                                self.C_LO, self.C_HI, _p(self.start), self.start.stride(1), self._st())
             if st != 0:
-                raise GsyeigError(st, "ws_decode")
-            opts.update(start_weights=self.weights, filter_degree=self.degree, filter_cut=float(self.cut.item()),
-                        filter_edge=float(self.prev[-1][2]["tnorm"]))
+                raise GsyeigError(st, "ws_extrapolate")
+            opts.update(start_block=self.start, start_weights=self.weights)
         sol.set_options(**opts)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        w, X, info = sol.solve(A, B, s, allow_unconverged=True)
-        fallback = 0
-        if info["status"] != 0 and opts["start_block"] is not None:
-            # the proposal did not converge: random start (the residual test decides)
-            sol.set_options(start_block=None, start_weights=None, filter_degree=0)
-            m0 = info["matvecs"]
-            w, X, info = sol.solve(A, B, s)
-            info["matvecs"] += m0
-            fallback = 1
+        w, X, info = sol.solve(A, B, s)
         e1.record()
         torch.cuda.synchronize()
-        info["fallback"] = fallback
-        self.prev = (self.prev + [(w, X, info)])[-2:]
+        self.prev = (self.prev + [(w, X)])[-2:]
         return w, X, info, e0.elapsed_time(e1)
 
-    def overlaps(self, X_next, X, B):
-        """P = X_next^T B X (s x s) on the library's GEMM engine (B symmetric:
-        its transpose is the same matrix, in column-major storage)."""
-        BX = self.solver.gemm(B.t(), X)
-        return self.solver.gemm(X_next, BX, transA=True)
 
-    def targets(self, w_next, scal, P, out):
-        st = self.lib.gsyeig_ws_targets(self.s, _p(w_next), _p(scal), _p(P), P.stride(1), _p(out), _stream(self.dev))
-        if st != 0:
-            raise GsyeigError(st, "ws_targets")
-        return out
+def evaluate_sequence(pencil, B, n: int, s: int, T: int, T_train: int, iters: int = 2000, lr: float = 1e-3,
+                      check=None, device=0, seed: int = 0):
+    """The warm-start experiment on a sequence: ``pencil(k)`` returns
+    (A_k, B, lam_k).  Problems 0..T_train-1 are solved with the plain random
+    start; the network is trained on them (features of t, B-optimal
+    extrapolation coefficients from t-1, t, t+1); problems T_train..T-1 are
+    then solved by the three methods, each from its own previous solutions.
+    ``check(A, B, w, X, lam)`` (optional; lam the whole constructed spectrum,
+    ascending) is called on every solution.
+    Returns (totals {method: [operator applications, ms, restarts]},
+    training loss history, ms of the training)."""
+    runs = {m: SequenceSolver(s, m, B, device=device) for m in ("random", "reuse", "learned")}
+    collect = runs["random"]
+    dev = collect.dev
+    sols = []
+    for k in range(T_train):
+        A, Bk, lam = pencil(k)
+        w, X, info, _ = collect.solve(A, Bk)
+        if check:
+            check(A, Bk, w, X, lam)
+        sols.append((w, X))
+    feats, targs = [], []
+    for k in range(1, T_train - 1):
+        feats.append(collect.features(sols[k][0], sols[k - 1][0], sols[k][1], sols[k - 1][1]).clone())
+        targs.append(collect.targets(sols[k - 1][1], sols[k][1], sols[k + 1][1],
+                                     torch.empty(s, device=dev, dtype=torch.float32)).clone())
+    Xf, Tf = torch.stack(feats), torch.stack(targs)
+    net = Mlp(3 * s + 1, s, seed=seed, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = net.train(Xf, Tf, iters, lr=lr)
+    e1.record()
+    torch.cuda.synchronize()
+    runs["learned"].mlp = net
+    # one untimed solve per method (problem T_train - 1 again) so that no
+    # method's first-call set-up falls into its times
+    A, Bk, _ = pencil(T_train - 1)
+    for m in ("reuse", "learned"):
+        runs[m].prev = [sols[-3], sols[-2]]
+        runs[m].solve(A, Bk)
+        runs[m].prev = [sols[-2], sols[-1]]
+    stats = {m: [0, 0.0, 0] for m in runs}
+    for k in range(T_train, T):
+        A, Bk, lam = pencil(k)
+        for m, r in runs.items():
+            w, X, info, ms = r.solve(A, Bk)
+            if check:
+                check(A, Bk, w, X, lam)
+            stats[m][0] += info["matvecs"]
+            stats[m][1] += ms
+            stats[m][2] += info["restarts"]
+    return stats, hist, e0.elapsed_time(e1)

@@ -197,6 +197,30 @@ def test_solve_inverse_falls_back_to_direct_route():
         _check_pairs(A, B, _np(w), _np(X), w_or, lam, f"fallback {which}")
 
 
+def test_solve_inverse_fallback_after_outer_updates():
+    """opts.inverse = 1 with A = U_A^T D U_A (U_A unit upper triangular, so
+    the Cholesky pivots of A are exactly D) and one negative entry of D at
+    column 700: the factorisation of A fails only after the first 512-column
+    outer block has been factored and its rank-512 update written into the
+    trailing matrix; the solve restores A, takes the direct route and returns
+    the oracle's pairs."""
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = 1024, 8
+    r = np.random.default_rng(21)
+    Ua = np.eye(n) + np.triu(r.standard_normal((n, n)) * (0.3 / np.sqrt(n)), 1)
+    d = r.uniform(1.0, 100.0, n)
+    d[700] = -50.0
+    A = Ua.T @ (d[:, None] * Ua)
+    A = 0.5 * (A + A.T)
+    _, B, _ = (t.numpy() for t in inputs.make_pencil(n, seed=21))
+    w_or, X_or = oracle.gsyeig(A, B, s)
+    assert w_or[0] < 0 < w_or[1]
+    w, X, info = Solver(0, inverse=1).solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s)
+    assert info["inverse"] == 0
+    _check_pairs(A, B, _np(w), _np(X), w_or, w_or, "fallback after outer updates")
+
+
 @pytest.mark.parametrize("inverse", [0, 1], ids=["direct", "inverse"])
 def test_solve_preserve_inputs_and_verify(inverse):
     """opts.preserve_inputs leaves device A and B bit for bit as they were;
@@ -520,18 +544,23 @@ def test_solve_implicit_variant_ki_matches_oracle(n, s, inverse):
     assert np.array_equal(G, G0), "KI must leave the untransformed matrix as it was"
 
 
+@pytest.mark.parametrize("mixed", [1, 2])
 @pytest.mark.parametrize("n,s,inverse", [(1024, 16, 1), (2048, 32, 1), (1000, 12, 1), (768, 8, 0)])
-def test_solve_mixed_precision_matches_oracle(n, s, inverse):
+def test_solve_mixed_precision_matches_oracle(n, s, inverse, mixed):
     """opts.mixed: block Lanczos (block 16) on the fp32 operator with fp32
-    accumulation, FP64 reorthogonalisation, then the FP64 block refinement
-    on C; the oracle's pairs at the same 1e-10 gates as the FP64 path."""
+    accumulation, FP64 reorthogonalisation, then the FP64 stage on C (1:
+    Lanczos from the fp32 Ritz vectors; 2: block refinement); the oracle's
+    pairs at the same 1e-10 gates as the FP64 path."""
     from paper_1111_6374_gb300 import Solver
 
     A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=n + s + 5))
     w_or, X_or = oracle.gsyeig(A, B, s)
-    w, X, info = Solver(0, mixed=1, inverse=inverse).solve(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s)
+    w, X, info = Solver(0, mixed=mixed, inverse=inverse).solve(torch.from_numpy(A).cuda(),
+                                                               torch.from_numpy(B).cuda(), s)
     assert info["inverse"] == inverse and info["nconv"] >= s
     assert info["block_steps"] > 0 and info["refine_iters"] >= 0
+    if mixed == 2 and inverse:  # the block refinement itself reaches the tolerance there
+        assert info["refine_fallback"] == 0 and info["refine_stop"] == 0, info
     w, X = _np(w), _np(X)
     cn = np.abs(lam).max()
     assert np.all(np.abs(w - w_or) <= 1e-10 * np.abs(w_or) + (0 if inverse else 1e-14 * cn))
