@@ -132,9 +132,9 @@ typedef struct {
    * fp32 accumulation, FP64 reorthogonalisation (CGS2) and projected matrix, giving the k = s +
    * max(16, s/8) Ritz vectors of the band matrix (krylov_dim is the block Krylov dimension, default
    * max(3s, s + 64) for mixed = 1 and max(5s, s + 64) for mixed = 2, rounded up to 16).  Then:
-   * 1: the FP64-accurate Lanczos (ke1 on the double-float operator) started from the sum of the s
-   *    wanted fp32 Ritz vectors, with Ritz tests every check_every steps (16 if 0), so that it stops
-   *    once the s pairs meet the tolerance;
+   * 1: the FP64-accurate Lanczos (ke1 on the double-float operator) started from the sum of the k
+   *    fp32 Ritz vectors, with Ritz tests every check_every steps (16 if 0), so that it stops once
+   *    the s pairs meet the tolerance;
    * 2: an FP64 block refinement (LOBPCG on the k vectors, Rayleigh-Ritz on an orthonormal [X, P, W]
    *    with the products by C on the FP64-accurate tensor-core engine) until the s wanted residuals
    *    meet tol ||C||; if it cannot, the FP64 Lanczos stage runs from a random start (info

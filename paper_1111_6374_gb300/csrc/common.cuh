@@ -175,6 +175,10 @@ struct FactorWork {
   double *UinvO = nullptr;
   double *panelO = nullptr;
   bool outer_ready = false;  // UinvO holds the current factor's outer inverses
+  // look-ahead of potrf (NULL: none): a second stream for the diagonal-block
+  // kernels and two events (the next diagonal block updated; it is factored)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_upd = nullptr, ev_diag = nullptr;
 };
 
 // order NB of the outer blocks of the blocked factorisations for inner width nb

@@ -220,20 +220,55 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
   GS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
   w.outer_ready = false;
   const int64_t NB = outer_block(nb);
-  for (int64_t J0 = 0; J0 < n; J0 += NB) {
+  // Look-ahead (w.side set): the diagonal-block kernels are FP64-bound on a
+  // few SMs and lie on the serial chain.  Each time the next diagonal block
+  // is about to be reached, it is updated first (a small GEMM), factored and
+  // inverted on the side stream, while the main stream applies the rest of
+  // the same update with the persistent GEMM kept off kDiagSMs SMs.
+  const bool la = w.side != nullptr && w.ev_upd != nullptr && w.ev_diag != nullptr;
+  constexpr int kDiagSMs = 9;  // k_potrf_diag (1 CTA) + k_trtri_cols (8 CTAs)
+  GemmContext *gc = current_gemm();
+  const int ctas0 = gc ? gc->max_ctas : 0;
+  auto reserve = [&](bool on) {
+    if (!gc) return;
+    const int cap = std::max(1, num_sms_cached() - kDiagSMs);
+    gc->max_ctas = on ? (ctas0 > 0 ? std::min(ctas0, cap) : cap) : ctas0;
+  };
+  // U_kk and U_kk^-1 of the diagonal block at k0 (order kb) on stream s
+  auto diag = [&](cudaStream_t s, int64_t k0, int kb) -> int {
+    double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
+    KernelProfiler *prof = current_profiler();
+    const size_t e0 = prof ? prof->start(s) : SIZE_MAX;
+    k_potrf_diag<<<1, DIAG_THREADS, sm, s>>>(B, ldb, k0, kb, nb, w.rdiag, w.flag);
+    k_trtri_cols<<<dim3((unsigned)ceil_div(nb, INV_WARPS), 1), INV_WARPS * 32, sm, s>>>(n, B, ldb, k0, nb, w.rdiag,
+                                                                                        Uinv_k, w.flag);
+    count_launch(2);
+    GS_CHECK_LAUNCH();
+    if (prof) prof->stop(s, e0, PROF_DIAG, 0.0, 0.0);
+    return GSYEIG_SUCCESS;
+  };
+  // the diagonal block at k1 (order kb1) once the main stream has updated it
+  auto diag_ahead = [&](int64_t k1, int kb1) -> int {
+    GS_CUDA(cudaEventRecord(w.ev_upd, st));
+    GS_CUDA(cudaStreamWaitEvent(w.side, w.ev_upd, 0));
+    GS_TRY(diag(w.side, k1, kb1));
+    GS_CUDA(cudaEventRecord(w.ev_diag, w.side));
+    return GSYEIG_SUCCESS;
+  };
+  bool ahead = false;  // the current diagonal block was factored on the side stream
+  int rc = GSYEIG_SUCCESS;
+  for (int64_t J0 = 0; J0 < n && rc == GSYEIG_SUCCESS; J0 += NB) {
     const int64_t J1 = std::min(n, J0 + NB);
     for (int64_t k0 = J0; k0 < J1; k0 += nb) {
       const int kb = (int)std::min<int64_t>(nb, J1 - k0);
       double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
       // U_kk (one CTA), then U_kk^-1 (one warp per column, many SMs)
-      KernelProfiler *prof = current_profiler();
-      const size_t e0 = prof ? prof->start(st) : SIZE_MAX;
-      k_potrf_diag<<<1, DIAG_THREADS, sm, st>>>(B, ldb, k0, kb, nb, w.rdiag, w.flag);
-      k_trtri_cols<<<dim3((unsigned)ceil_div(nb, INV_WARPS), 1), INV_WARPS * 32, sm, st>>>(n, B, ldb, k0, nb, w.rdiag,
-                                                                                         Uinv_k, w.flag);
-      count_launch(2);
-      GS_CHECK_LAUNCH();
-      if (prof) prof->stop(st, e0, PROF_DIAG, 0.0, 0.0);
+      if (ahead) {
+        GS_CUDA(cudaStreamWaitEvent(st, w.ev_diag, 0));
+        ahead = false;
+      } else {
+        GS_TRY(diag(st, k0, kb));
+      }
       const int64_t rest = n - k0 - kb;
       if (rest <= 0) break;
       double *Bk = &B[GS_IDX(k0, k0 + kb, ldb)];
@@ -242,17 +277,60 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
       GS_TRY(copy_block(st, kb, rest, w.panel, kb, Bk, ldb, w.flag));
       // rows of the outer block below this step: B (upper) -= U_k,.^T U_k,.
       const int64_t rin = J1 - k0 - kb;
-      if (rin > 0)
-        GS_TRY(dgemm(st, true, false, rin, rest, kb, -1.0, w.panel, kb, w.panel, kb, 1.0,
-                     &B[GS_IDX(k0 + kb, k0 + kb, ldb)], ldb, TRI_UPPER, 0, w.flag));
+      if (rin <= 0) continue;
+      const int64_t k1 = k0 + kb;
+      double *Bn = &B[GS_IDX(k1, k1, ldb)];
+      if (!la) {
+        GS_TRY(dgemm(st, true, false, rin, rest, kb, -1.0, w.panel, kb, w.panel, kb, 1.0, Bn, ldb, TRI_UPPER, 0,
+                     w.flag));
+        continue;
+      }
+      // the next diagonal block first, then the rest of the update beside its factorisation
+      const int64_t kb1 = std::min<int64_t>(nb, rin);
+      GS_TRY(dgemm(st, true, false, kb1, kb1, kb, -1.0, w.panel, kb, w.panel, kb, 1.0, Bn, ldb, TRI_UPPER, 0, w.flag));
+      GS_TRY(diag_ahead(k1, (int)kb1));
+      ahead = true;
+      reserve(true);
+      if (rest > kb1)
+        rc = dgemm(st, true, false, kb1, rest - kb1, kb, -1.0, w.panel, kb, w.panel + (size_t)kb1 * kb, kb, 1.0,
+                   &B[GS_IDX(k1, k1 + kb1, ldb)], ldb, TRI_ALL, 0, w.flag);
+      if (rc == GSYEIG_SUCCESS && rin > kb1)
+        rc = dgemm(st, true, false, rin - kb1, rest - kb1, kb, -1.0, w.panel + (size_t)kb1 * kb, kb,
+                   w.panel + (size_t)kb1 * kb, kb, 1.0, &B[GS_IDX(k1 + kb1, k1 + kb1, ldb)], ldb, TRI_UPPER, 0,
+                   w.flag);
+      reserve(false);
+      if (rc != GSYEIG_SUCCESS) break;
     }
+    if (rc != GSYEIG_SUCCESS) break;
     // trailing matrix beyond the outer block (upper) -= U_J,rest^T U_J,rest
     const int64_t r2 = n - J1;
-    if (r2 > 0)
-      GS_TRY(dgemm(st, true, false, r2, r2, J1 - J0, -1.0, &B[GS_IDX(J0, J1, ldb)], ldb, &B[GS_IDX(J0, J1, ldb)], ldb,
-                   1.0, &B[GS_IDX(J1, J1, ldb)], ldb, TRI_UPPER, 0, w.flag));
+    if (r2 <= 0) break;
+    const double *UJ = &B[GS_IDX(J0, J1, ldb)];
+    if (!la) {
+      GS_TRY(dgemm(st, true, false, r2, r2, J1 - J0, -1.0, UJ, ldb, UJ, ldb, 1.0, &B[GS_IDX(J1, J1, ldb)], ldb,
+                   TRI_UPPER, 0, w.flag));
+      continue;
+    }
+    // the first diagonal block of the next outer block first, as above
+    const int64_t kbn = std::min<int64_t>(nb, r2);
+    GS_TRY(dgemm(st, true, false, kbn, kbn, J1 - J0, -1.0, UJ, ldb, UJ, ldb, 1.0, &B[GS_IDX(J1, J1, ldb)], ldb,
+                 TRI_UPPER, 0, w.flag));
+    GS_TRY(diag_ahead(J1, (int)kbn));
+    ahead = true;
+    reserve(true);
+    if (r2 > kbn) {
+      const double *UJn = &B[GS_IDX(J0, J1 + kbn, ldb)];
+      rc = dgemm(st, true, false, kbn, r2 - kbn, J1 - J0, -1.0, UJ, ldb, UJn, ldb, 1.0, &B[GS_IDX(J1, J1 + kbn, ldb)],
+                 ldb, TRI_ALL, 0, w.flag);
+      if (rc == GSYEIG_SUCCESS)
+        rc = dgemm(st, true, false, r2 - kbn, r2 - kbn, J1 - J0, -1.0, UJn, ldb, UJn, ldb, 1.0,
+                   &B[GS_IDX(J1 + kbn, J1 + kbn, ldb)], ldb, TRI_UPPER, 0, w.flag);
+    }
+    reserve(false);
   }
-  return GSYEIG_SUCCESS;
+  // every diagonal block factored on the side stream is ordered before the caller's next step
+  if (ahead) GS_CUDA(cudaStreamWaitEvent(st, w.ev_diag, 0));
+  return rc;
 }
 
 // The outer-block inverses U_JJ^-1 of every outer block (have_uinv: the

@@ -40,14 +40,26 @@ namespace {
 
 using slicing::S;
 using slicing::EXP_NONE;
-constexpr int UM = 128, UN = 32, UKS = 32;  // tile rows, tile cols, K per stage
+#ifndef UMMA_UKS
+#define UMMA_UKS 32
+#endif
+#ifndef UMMA_NBUF
+#define UMMA_NBUF 3
+#endif
+constexpr int UM = 128, UN = 32, UKS = UMMA_UKS;  // tile rows, tile cols, K per stage (16 or 32)
 constexpr int KB2 = UKS / 16;                // k16 blocks per stage
 constexpr int KPAD = 32;                     // K padding of the digit planes
 constexpr int A_K16_BYTES = UM * 16 * 2;     // one slice, one k16 block: 4096
 constexpr int B_K16_BYTES = UN * 16 * 2;     // 1024
 constexpr int A_STAGE = KB2 * S * A_K16_BYTES;  // 57344
 constexpr int B_STAGE = KB2 * S * B_K16_BYTES;  // 14336
-constexpr int NBUF = 3;
+constexpr int NBUF = UMMA_NBUF;  // stages in the ring
+static_assert(UKS == 16 || UKS == 32, "a stage is one or two k16 blocks");
+// after the ring: full[NBUF], empty[NBUF], acc_full[2], acc_empty[2], fin (8 bytes each), the TMEM
+// slot (4 bytes), rounded up to 16
+constexpr int BAR_BYTES = (((2 * NBUF + 5) * 8 + 4) + 15) / 16 * 16;
+constexpr size_t UMMA_SMEM = (size_t)NBUF * (KB2 * S * (UM + UN) * 32) + BAR_BYTES;
+static_assert(UMMA_SMEM <= 227 * 1024 - 1024, "the stage ring and its barriers exceed shared memory");
 constexpr int CH_STAGES = 128 / UKS;  // K stages per exact chunk (level sums exact for K <= 128)
 constexpr int UMMA_MAX_K = 512;
 constexpr int TMEM_COLS = 512;
@@ -257,12 +269,20 @@ constexpr int EPI_COLS = UN / (EPI_WARPS / 4);  // columns of a tile per epilogu
 // Exact integer value of a level sum (an integer-valued fp32, |x| < 2^24).
 __device__ __forceinline__ int32_t lvl(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
+// The same for |x| <= 2^22 without the conversion unit (16 per clock per SM
+// on GB300): x + 1.5 2^23 lies in [2^23, 2^24], where every integer is an
+// fp32, so the addition is exact and the bit pattern minus that of 1.5 2^23
+// is x.  Levels 0 and 1 of a K <= 128 chunk qualify (|L_d| <= (d + 1) 2^21).
+__device__ __forceinline__ int32_t lvl22(uint32_t bits) {
+  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
+}
+
 // (vh:vl) += V for the 7 level sums v[0..6] of one element,
 // V = sum_d L_d 256^(6-d), |L_d| <= (d + 1) 128 2^14 (K <= 128 per chunk):
 // a = L0 256 + L1 and b = L2 256 + L3 fit in int32, P = a 2^16 + b < 2^47,
 // Q = (L4 256 + L5) 256 + L6 < 2^41, V = P 2^24 + Q.
 __device__ __forceinline__ void fold_add(const uint32_t (&v)[S], int32_t &vh, uint64_t &vl) {
-  const int32_t a = lvl(v[0]) * 256 + lvl(v[1]);
+  const int32_t a = lvl22(v[0]) * 256 + lvl22(v[1]);
   const int32_t b = lvl(v[2]) * 256 + lvl(v[3]);
   const int64_t P = (int64_t)a * 65536 + (int64_t)b;
   const int64_t Q = ((int64_t)lvl(v[4]) * 256 + (int64_t)lvl(v[5])) * 256 + (int64_t)lvl(v[6]);
@@ -563,7 +583,7 @@ int umma_gemm(cudaStream_t st, bool transA, bool transB, int64_t M, int64_t N, i
   P.SB = P.SA + (size_t)S * Mpad * Kpad * 2;
   slicing::slice_layout(P, reinterpret_cast<int *>(P.SB + (size_t)S * Npad * Kpad * 2));
   GS_TRY(slicing::slice_operands(st, transA, transB, M, N, K, A, lda, B, ldb, P, {true, UM}, {true, UN}));
-  const size_t smem = (size_t)NBUF * (A_STAGE + B_STAGE) + 128;
+  const size_t smem = UMMA_SMEM;
   GS_TRY(set_max_smem((const void *)k_sliced_umma, (int)smem));
   TileGrid g{M, N, diag, (int)(Mpad / UM), (int)(Npad / UN), (int)mode};
   // CTAs without an active tile (TRI modes) only set up and leave

@@ -59,8 +59,10 @@ struct gsyeig_ctx {
   DevBuf uinvO;           // inverses of the outer diagonal blocks and the outer panel staging
   DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts, arrow;
   DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
+  cudaStream_t side = nullptr;  // look-ahead of potrf: the diagonal-block kernels
+  cudaEvent_t side_ev[2] = {};
   cudaStream_t cp = nullptr;  // host-pointer calls: the copy of the matrix needed second
-  cudaEvent_t cp_ev = nullptr;
+  cudaEvent_t cp_ev = nullptr, cp_first = nullptr;
   DevBuf pA, pB;          // working copies when opts.preserve_inputs
   DevBuf vA, vB, vws;     // originals and workspace of opts.verify
   DevBuf gemm_ws;         // slices of the tensor-core GEMM
@@ -218,6 +220,13 @@ int factor_ws(gsyeig_handle h, int64_t n, int nb, int64_t s, FactorWork &w) {
   w.panel = h->panel.d();
   w.flag = static_cast<int *>(h->flag.p);
   w.rdiag = reinterpret_cast<double *>(static_cast<char *>(h->flag.p) + 256);
+  if (!h->side) {
+    GS_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : h->side_ev) GS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  w.side = h->side;
+  w.ev_upd = h->side_ev[0];
+  w.ev_diag = h->side_ev[1];
   return GSYEIG_SUCCESS;
 }
 
@@ -748,11 +757,12 @@ int cholqr2(gsyeig_handle h, cudaStream_t st, int64_t n, int64_t b, double *Z, i
 // max(8, s/4) random guard columns, and ||C|| is bounded by its 1-norm.
 //
 // With stage_out != NULL (opts.mixed = 1) the function stops after the fp32
-// stage: *stage_out = the s wanted Ritz vectors of the band matrix (n x s,
-// ld n, in the handle's workspace), the start of the FP64 Lanczos stage.
+// stage: *stage_out = the k = s + guard Ritz vectors of the band matrix at
+// the wanted end (n x k, ld n, in the handle's workspace), the start of the
+// FP64 Lanczos stage, and *stage_cols = k.
 int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int64_t s, int which, double *theta_out,
                   double *Y, int64_t ldy, gsyeig_info *info, double *ms_ke3, const double *F = nullptr,
-                  int64_t ldf = 0, const double **stage_out = nullptr) {
+                  int64_t ldf = 0, const double **stage_out = nullptr, int64_t *stage_cols = nullptr) {
   cudaStream_t st = h->st;
   constexpr int BK = 16;
   const gsyeig_opts &o = h->opts;
@@ -877,7 +887,8 @@ int lanczos_mixed(gsyeig_handle h, const double *C, int64_t ldc, int64_t n, int6
   (void)gc0;
   GS_CUDA(cudaEventRecord(ev1, st));
   if (stage_out) {
-    *stage_out = Sb + (size_t)((which == GSYEIG_LARGEST) ? k - s : 0) * n;
+    *stage_out = Sb;
+    if (stage_cols) *stage_cols = k;
     GS_CUDA(cudaStreamSynchronize(st));
     if (info) {
       info->block_steps = blocks;
@@ -1133,7 +1144,11 @@ int gsyeig_destroy(gsyeig_handle h) {
   for (gsyeig_ctx *sub : h->subs) gsyeig_destroy(sub);
   for (auto &e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->side_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->cp_ev) cudaEventDestroy(h->cp_ev);
+  if (h->cp_first) cudaEventDestroy(h->cp_first);
   if (h->cp) cudaStreamDestroy(h->cp);
   if (h->st) cudaStreamDestroy(h->st);
   delete h;
@@ -1378,12 +1393,14 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     dX = h->hX.d();
     dlda = dldb = dldx = n;
     // the matrix factored first (A on the inverse route, else B) on the
-    // solve's stream; the other on a second stream, so that its transfer
-    // overlaps the Cholesky factorisation; the solve waits for it just
-    // before its first read
+    // solve's stream; the other on a second stream once the first has landed
+    // (the two would otherwise share the link and delay the factorisation),
+    // so that its transfer overlaps the Cholesky factorisation; the solve
+    // waits for it just before its first read
     if (!h->cp) {
       GS_CUDA(cudaStreamCreateWithFlags(&h->cp, cudaStreamNonBlocking));
       GS_CUDA(cudaEventCreateWithFlags(&h->cp_ev, cudaEventDisableTiming));
+      GS_CUDA(cudaEventCreateWithFlags(&h->cp_first, cudaEventDisableTiming));
     }
     const bool a_first = h->opts.inverse == 1 && which == GSYEIG_SMALLEST;
     double *d1 = a_first ? dA : dB, *d2 = a_first ? dB : dA;
@@ -1391,7 +1408,8 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     const int64_t l1 = a_first ? lda : ldb, l2 = a_first ? ldb : lda;
     GS_CUDA(cudaMemcpy2DAsync(d1, n * sizeof(double), s1, l1 * sizeof(double), n * sizeof(double), n,
                               cudaMemcpyHostToDevice, st));
-    GS_CUDA(cudaStreamWaitEvent(h->cp, h->ev[0], 0));  // the staging buffer is free once the call has begun
+    GS_CUDA(cudaEventRecord(h->cp_first, st));
+    GS_CUDA(cudaStreamWaitEvent(h->cp, h->cp_first, 0));
     GS_CUDA(cudaMemcpy2DAsync(d2, n * sizeof(double), s2, l2 * sizeof(double), n * sizeof(double), n,
                               cudaMemcpyHostToDevice, h->cp));
     GS_CUDA(cudaEventRecord(h->cp_ev, h->cp));
@@ -1505,18 +1523,22 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     // (default 16) steps: the start vector lies in the wanted invariant
     // subspace up to the fp32 stage's error, so the FP64 stage stops early
     const double *blk = nullptr;
+    int64_t bcols = 0;
     status = lanczos_mixed(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
-                           nullptr, 0, &blk);
+                           nullptr, 0, &blk, &bcols);
     if (status != GSYEIG_SUCCESS && status != GSYEIG_NOT_SUPPORTED) return status;
     gsyeig_info keep{};
     if (info) keep = *info;
     const gsyeig_opts saved = h->opts;
     if (status == GSYEIG_SUCCESS) {
-      GS_TRY(h->mx_ones.ensure((size_t)s * sizeof(double)));
-      const std::vector<double> ones((size_t)s, 1.0);
-      GS_CUDA(cudaMemcpyAsync(h->mx_ones.p, ones.data(), (size_t)s * sizeof(double), cudaMemcpyHostToDevice, st));
+      // every Ritz vector of the fp32 stage, guard columns included: the
+      // Lanczos stage then resolves s + guard pairs, and the wanted s see
+      // the wider gap to the first pair outside that set
+      GS_TRY(h->mx_ones.ensure((size_t)bcols * sizeof(double)));
+      const std::vector<double> ones((size_t)bcols, 1.0);
+      GS_CUDA(cudaMemcpyAsync(h->mx_ones.p, ones.data(), (size_t)bcols * sizeof(double), cudaMemcpyHostToDevice, st));
       h->opts.start_block = blk;
-      h->opts.start_cols = s;
+      h->opts.start_cols = bcols;
       h->opts.ld_start = n;
       h->opts.start_weights = h->mx_ones.d();
       h->opts.filter_degree = 0;
@@ -1568,7 +1590,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     GS_CUDA(cudaMemcpyAsync(&mu_lo, h->hw.d(), sizeof(double), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaMemcpyAsync(&mu_hi, h->hw.d() + (s - 1), sizeof(double), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
-    if (mu_lo > 0.0 && theta_min > 0.0 && mu_hi > 1e3 * mu_lo)
+    if (mu_lo > 0.0 && theta_min > 0.0 && mu_hi > 1e5 * mu_lo)
       GS_TRY(b_orthonormalise_inverse(h, st, n, s, dG, dldg, dX, dldx, h->hw.d()));
   }
   GS_CUDA(cudaEventRecord(h->ev[4], st));

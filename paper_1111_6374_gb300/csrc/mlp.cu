@@ -1,10 +1,11 @@
 // The learned warm start for sequences of related problems (the paper's
 // Section 3 motivates them with the dozens of related eigenproblems of each
 // DFT self-consistency cycle).  A small MLP (n_in -> 256 -> 256 -> n_out,
-// ReLU) reads the previous problem's Ritz values and parameter step and
-// proposes the next problem's start block (one weight per previous
-// eigenvector) and the cut of a Chebyshev filter; the solver's residual test
-// alone decides acceptance.
+// ReLU) reads the previous two problems' eigenvalues and the overlaps of
+// their eigenvectors and predicts, per wanted pair, how far to extrapolate
+// the eigenvector along the sequence; the extrapolated block builds the next
+// solve's start vector, and the solver's residual test alone decides
+// acceptance.
 //
 // Every GEMM of the network's forward and backward pass runs on the bf16
 // tensor cores (tcgen05.mma kind::f16, fp32 accumulation in TMEM).  The

@@ -15,7 +15,8 @@
 // NT - 1 - i tiles below the diagonal in its column, NT tiles for every CTA
 // (balanced), and writes its 64 rows once: no atomics, no partial sums in
 // memory, deterministic.  Each tile is read twice in all (8 n^2 bytes per
-// product); the kernel is bound by the fp32 FMA rate (32 n^2 FMAs).
+// product), through a two-deep ring of asynchronous 16-byte copies so that
+// the next tile and W slice land while the current ones are used.
 #include "mixed.cuh"
 
 namespace gs {
@@ -88,32 +89,52 @@ __global__ void k_from_f32(int64_t n, const float *__restrict__ Z32, const unsig
   }
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+// The tile and W slice of step `step` of block row i into shared buffer b
+// (asynchronous 16-byte copies, one commit group).
+__device__ __forceinline__ void s32_prefetch(int i, int step, const float *__restrict__ T, const float *__restrict__ W,
+                                             float *tile, float *wj) {
+  const int j = step;
+  const bool row = step <= i;
+  const int bi = row ? i : j, bj = row ? j : i;
+  const float *src = T + ((int64_t)bi * (bi + 1) / 2 + bj) * TS * TS;
+  for (int idx = threadIdx.x; idx < TS * TS / 4; idx += S32_THREADS) cp_async16(tile + 4 * idx, src + 4 * idx);
+  const float *ws = W + (int64_t)j * TS * NB;
+  for (int idx = threadIdx.x; idx < TS * NB / 4; idx += S32_THREADS) cp_async16(wj + 4 * idx, ws + 4 * idx);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 __global__ void __launch_bounds__(S32_THREADS) k_symm32(int NT, const float *__restrict__ T, const float *__restrict__ W,
                                                         float *__restrict__ Z) {
-  __shared__ float tile[TS * TS];
-  __shared__ float4 wj[TS][NB / 4];
+  // two buffers: the copies of step + 1 run while step is computed
+  __shared__ __align__(16) float tile[2][TS * TS];
+  __shared__ __align__(16) float wj[2][TS * NB];
   const int i = blockIdx.x;
   const int t = threadIdx.x, r = t % TS, q = t / TS;  // 4 column quads
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  s32_prefetch(i, 0, T, W, tile[0], wj[0]);
   for (int step = 0; step < NT; step++) {
-    // steps 0..i: row tiles (i, j = step); then column tiles (j = step, i), j > i
-    const bool row = step <= i;
-    const int j = step;
-    const int bi = row ? i : j, bj = row ? j : i;
-    const float *src = T + ((int64_t)bi * (bi + 1) / 2 + bj) * TS * TS;
-    __syncthreads();  // the previous tile is no longer read
-    for (int idx = t; idx < TS * TS / 4; idx += S32_THREADS)
-      reinterpret_cast<float4 *>(tile)[idx] = reinterpret_cast<const float4 *>(src)[idx];
-    for (int idx = t; idx < TS * NB / 4; idx += S32_THREADS)
-      wj[idx / (NB / 4)][idx % (NB / 4)] = reinterpret_cast<const float4 *>(W + (int64_t)j * TS * NB)[idx];
-    __syncthreads();
-    if (row) {
+    const int b = step & 1;
+    if (step + 1 < NT) {
+      s32_prefetch(i, step + 1, T, W, tile[b ^ 1], wj[b ^ 1]);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();  // every thread's copies of this step have landed
+    const float *tl = tile[b];
+    const float4 *wv = reinterpret_cast<const float4 *>(wj[b]);
+    if (step <= i) {
       // Z_i(r, 4q..4q+3) += sum_k C_ij(r, k) W_j(k, 4q..4q+3); a warp's lanes
       // read 32 rows of one column: distinct banks under the swizzle
 #pragma unroll 8
       for (int k = 0; k < TS; k++) {
-        const float c = tile[(r ^ (k & 31)) + TS * k];
-        const float4 w = wj[k][q];
+        const float c = tl[(r ^ (k & 31)) + TS * k];
+        const float4 w = wv[k * (NB / 4) + q];
         acc.x = fmaf(c, w.x, acc.x);
         acc.y = fmaf(c, w.y, acc.y);
         acc.z = fmaf(c, w.z, acc.z);
@@ -123,14 +144,15 @@ __global__ void __launch_bounds__(S32_THREADS) k_symm32(int NT, const float *__r
       // Z_i(r, .) += sum_k C_ji(k, r) W_j(k, .): column r of the stored tile
 #pragma unroll 8
       for (int k = 0; k < TS; k++) {
-        const float c = tile[(k ^ (r & 31)) + TS * r];
-        const float4 w = wj[k][q];
+        const float c = tl[(k ^ (r & 31)) + TS * r];
+        const float4 w = wv[k * (NB / 4) + q];
         acc.x = fmaf(c, w.x, acc.x);
         acc.y = fmaf(c, w.y, acc.y);
         acc.z = fmaf(c, w.z, acc.z);
         acc.w = fmaf(c, w.w, acc.w);
       }
     }
+    __syncthreads();  // buffer b is free for the copies of step + 2
   }
   reinterpret_cast<float4 *>(Z + ((int64_t)i * TS + r) * NB)[q] = acc;
 }
