@@ -133,7 +133,7 @@ typedef struct {
    * max(16, s/8) Ritz vectors of the band matrix (krylov_dim is the block Krylov dimension, default
    * max(3s, s + 64) for mixed = 1 and max(5s, s + 64) for mixed = 2, rounded up to 16).  Then:
    * 1: the FP64-accurate Lanczos (ke1 on the double-float operator) started from the sum of the k
-   *    fp32 Ritz vectors, with Ritz tests every check_every steps (16 if 0), so that it stops once
+   *    fp32 Ritz vectors, with Ritz tests every check_every steps (32 if 0), so that it stops once
    *    the s pairs meet the tolerance;
    * 2: an FP64 block refinement (LOBPCG on the k vectors, Rayleigh-Ritz on an orthonormal [X, P, W]
    *    with the products by C on the FP64-accurate tensor-core engine) until the s wanted residuals
@@ -153,6 +153,14 @@ typedef struct {
    * directly from the block F X0 plus max(8, s/4) random guard columns, with no Lanczos stage; for a
    * sequence of related problems whose eigenvectors move little from one problem to the next. */
   int32_t block_start;
+  /* With inverse = 1 and which = SMALLEST: solve the shifted pencil (A - shift B, B) on the inverse
+   * route, A - shift B = L^T L, and return lambda = shift + 1/mu.  A shift below the smallest
+   * eigenvalue makes A - shift B positive definite when A itself is not (Section 3.1's route then
+   * applies to any pencil whose smallest eigenvalue is known to lie above the shift).  The shift is
+   * applied to the upper triangle only (the part the Cholesky reads): if A - shift B is not positive
+   * definite, A's diagonal is restored and the unshifted direct route runs, reading A's untouched
+   * lower triangle.  0 (default): no shift. */
+  double shift;
 } gsyeig_opts;
 
 /* Per-solve report.  Stage times are CUDA-event milliseconds per paper key
@@ -367,6 +375,17 @@ int gsyeig_ws_coef_targets(int64_t n, int64_t s, const double *D, int64_t ldd, c
                            const double *BE, int64_t ldbe, double lo, double hi, float *targets, void *stream);
 int gsyeig_ws_extrapolate(int64_t n, int64_t s, const double *X, int64_t ldx, const double *D, int64_t ldd,
                           const float *coef, double lo, double hi, double *out, int64_t ldo, void *stream);
+/* The shift of the next solve (gsyeig_opts.shift, Section 3.1's inverse route on A - shift B): with
+ * the eigenvalues w_prev (ascending, s) and w_prev2 of the previous two problems,
+ * gsyeig_ws_shift writes shift[0] = w_prev[0] + clamp(coef[0], lo, hi) (w_prev[0] - w_prev2[0])
+ * - frac (w_prev[s-1] - w_prev[0]) / s, a margin of frac mean spacings below the extrapolated
+ * smallest eigenvalue (coef NULL: no extrapolation, w_prev2 may then be NULL).
+ * gsyeig_ws_shift_target writes the coefficient that would have extrapolated to w[0] exactly,
+ * clamped to [lo, hi] (0 when w_prev[0] = w_prev2[0]): the training target.  Device pointers. */
+int gsyeig_ws_shift(int64_t s, const double *w_prev2, const double *w_prev, const float *coef, double lo, double hi,
+                    double frac, double *shift, void *stream);
+int gsyeig_ws_shift_target(const double *w_prev2, const double *w_prev, const double *w, double lo, double hi,
+                           float *target, void *stream);
 
 /* ---- batches of independent problems ---------------------------------- */
 /* One problem of a batch: the arguments of gsyeig_solve (device pointers). */

@@ -45,7 +45,7 @@ class Opts(ctypes.Structure):
                 ("start_cols", ctypes.c_int64), ("ld_start", ctypes.c_int64), ("filter_cut", ctypes.c_double),
                 ("filter_edge", ctypes.c_double), ("filter_degree", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("mixed", ctypes.c_int32), ("graph", ctypes.c_int32), ("max_ctas", ctypes.c_int32),
-                ("block_start", ctypes.c_int32)]
+                ("block_start", ctypes.c_int32), ("shift", ctypes.c_double)]
 
 
 class Problem(ctypes.Structure):
@@ -122,6 +122,8 @@ def load(build_if_missing: bool = True):
         "gsyeig_ws_align": ([i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, vp], i32),
         "gsyeig_ws_coef_targets": ([i64, i64, vp, i64, vp, i64, vp, i64, dp, dp, vp, vp], i32),
         "gsyeig_ws_extrapolate": ([i64, i64, vp, i64, vp, i64, vp, dp, dp, vp, i64, vp], i32),
+        "gsyeig_ws_shift": ([i64, vp, vp, vp, dp, dp, dp, vp, vp], i32),
+        "gsyeig_ws_shift_target": ([vp, vp, vp, dp, dp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -1165,7 +1165,7 @@ int gsyeig_set_options(gsyeig_handle h, const gsyeig_opts *o) {
       o->preserve_inputs > 1 || o->verify < 0 || o->verify > 1 || o->implicit < 0 || o->implicit > 1 ||
       o->wait_limit < 0 || o->filter_degree < 0 || o->filter_degree > 64 || o->check_every < 0 ||
       o->start_cols < 0 || (o->start_block && o->start_cols > 0 && o->ld_start < 1) ||
-      (o->filter_degree > 0 && !(o->filter_cut != o->filter_edge)) || o->mixed < 0 || o->mixed > 2 ||
+      (o->filter_degree > 0 && !(o->filter_cut != o->filter_edge)) || o->mixed < 0 || o->mixed > 2 || !std::isfinite(o->shift) ||
       o->graph < 0 || o->graph > 1 || o->max_ctas < 0 || o->block_start < 0 || o->block_start > 1)
     return -2;
   if (o->krylov_dim > 0 && o->keep > 0 && o->keep >= o->krylov_dim) return -2;
@@ -1464,6 +1464,10 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     GS_TRY(h->diag.ensure((size_t)n * sizeof(double)));
     GS_CUDA(cudaMemcpy2DAsync(h->diag.p, sizeof(double), dA, (size_t)(dlda + 1) * sizeof(double), sizeof(double), n,
                               cudaMemcpyDeviceToDevice, st));
+    if (h->opts.shift != 0.0) {  // the upper triangle of A - shift B (B's upper triangle is the one read)
+      GS_TRY(second_ready());
+      GS_TRY(lz_shift_upper(st, n, dA, dlda, dB, dldb, h->opts.shift));
+    }
     GS_TRY(potrf_blocked(st, n, dA, dlda, nb, fw));
     GS_CUDA(cudaMemcpyAsync(&flag, fw.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
@@ -1519,9 +1523,9 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   int status;
   if (h->opts.mixed == 1) {
     // fp32 block Lanczos, then the FP64-accurate Lanczos started from the sum
-    // of the s wanted fp32 Ritz vectors, with Ritz tests every check_every
-    // (default 16) steps: the start vector lies in the wanted invariant
-    // subspace up to the fp32 stage's error, so the FP64 stage stops early
+    // of the fp32 Ritz vectors, with Ritz tests every check_every (default
+    // 32) steps: the start vector lies in the wanted invariant subspace up to
+    // the fp32 stage's error, so the FP64 stage stops early
     const double *blk = nullptr;
     int64_t bcols = 0;
     status = lanczos_mixed(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
@@ -1542,7 +1546,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
       h->opts.ld_start = n;
       h->opts.start_weights = h->mx_ones.d();
       h->opts.filter_degree = 0;
-      if (h->opts.check_every == 0) h->opts.check_every = 16;
+      if (h->opts.check_every == 0) h->opts.check_every = 32;
     }
     status = lanczos_run(h, dG, dldg, n, s, inv ? GSYEIG_LARGEST : which, h->hw.d(), dX, dldx, info, &ms_ke3,
                          nullptr, inv ? &theta_min : nullptr, nullptr, 0);
@@ -1603,7 +1607,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     GS_CUDA(cudaMemcpyAsync(&mu_min, h->hw.d(), sizeof(double), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
     if (!(mu_min > 0.0)) return GSYEIG_NOT_SPD;
-    GS_TRY(lz_invert_pairs(st, n, s, h->hw.d(), dX, dldx));
+    GS_TRY(lz_invert_pairs(st, n, s, h->hw.d(), dX, dldx, h->opts.shift));
   }
   GS_CUDA(cudaMemcpyAsync(w, h->hw.p, (size_t)s * sizeof(double), cudaMemcpyDefault, st));
   if (hostA)

@@ -185,12 +185,23 @@ __global__ void k_invert_cols(int64_t n, int64_t s, const double *__restrict__ t
 }
 
 // theta[i] <- 1 / theta[s-1-i] (one thread per pair)
-__global__ void k_invert_vals(int64_t s, double *theta) {
+// theta (mu ascending) <- shift + 1/mu, ascending
+__global__ void k_invert_vals(int64_t s, double *theta, double shift) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (s + 1) / 2; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t k = s - 1 - i;
     const double a = theta[i], b = theta[k];
-    theta[i] = 1.0 / b;
-    theta[k] = 1.0 / a;
+    theta[i] = shift + 1.0 / b;
+    theta[k] = shift + 1.0 / a;
+  }
+}
+
+// A(i, j) -= shift B(i, j) for i <= j (the upper triangles)
+__global__ void k_shift_upper(int64_t n, double *__restrict__ A, int64_t lda, const double *__restrict__ B,
+                              int64_t ldb, double shift) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    if (i <= j) A[i + j * lda] = fma(-shift, B[i + j * ldb], A[i + j * lda]);
   }
 }
 
@@ -290,10 +301,17 @@ int lz_finalize(cudaStream_t st, int64_t j, int64_t m, const double *h1, const d
   return GSYEIG_SUCCESS;
 }
 
-int lz_invert_pairs(cudaStream_t st, int64_t n, int64_t s, double *theta, double *X, int64_t ldx) {
+int lz_invert_pairs(cudaStream_t st, int64_t n, int64_t s, double *theta, double *X, int64_t ldx, double shift) {
   k_invert_cols<<<grid1d(n * ((s + 1) / 2), 256), 256, 0, st>>>(n, s, theta, X, ldx);
-  k_invert_vals<<<1, 128, 0, st>>>(s, theta);
+  k_invert_vals<<<1, 128, 0, st>>>(s, theta, shift);
   count_launch(2);
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int lz_shift_upper(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *B, int64_t ldb, double shift) {
+  k_shift_upper<<<grid1d(n * n, 256), 256, 0, st>>>(n, A, lda, B, ldb, shift);
+  count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;
 }

@@ -34,10 +34,13 @@ int lz_random(cudaStream_t st, int64_t n, uint64_t seed, uint64_t stream, double
 // and e[i] = 0 for i < k (S is m x k, ld m).
 int lz_thick_restart(cudaStream_t st, int64_t m, int64_t k, const double *theta, const double *S, double *d, double *e,
                      double *b);
-// Inverse problem (B x = mu A x, theta = its s largest mu, ascending) back to
-// (A, B): X column i <- X column s-1-i / sqrt(theta[s-1-i]) and
-// theta[i] <- 1 / theta[s-1-i], so lambda ascends and X^T B X = I.
-int lz_invert_pairs(cudaStream_t st, int64_t n, int64_t s, double *theta, double *X, int64_t ldx);
+// Inverse problem (B x = mu (A - shift B) x, theta = its s largest mu,
+// ascending) back to (A, B): X column i <- X column s-1-i /
+// sqrt(theta[s-1-i]) and theta[i] <- shift + 1 / theta[s-1-i], so lambda
+// ascends and X^T B X = I.
+int lz_invert_pairs(cudaStream_t st, int64_t n, int64_t s, double *theta, double *X, int64_t ldx, double shift = 0.0);
+// A(i, j) -= shift B(i, j) over the upper triangles (i <= j)
+int lz_shift_upper(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *B, int64_t ldb, double shift);
 // out = X w (X n x k, ld ldx; w device, k entries, NULL = all ones).
 int lz_weighted_sum(cudaStream_t st, int64_t n, int64_t k, const double *X, int64_t ldx, const double *w,
                     double *out);

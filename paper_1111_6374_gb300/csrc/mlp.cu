@@ -307,6 +307,28 @@ __global__ void k_ws_extrapolate(int64_t n, int s, const double *__restrict__ X,
     out[i + (int64_t)j * ldo] = X[i + (int64_t)j * ldx] - cj * D[i + (int64_t)j * ldd];
 }
 
+// the extrapolation coefficient of the smallest eigenvalue along the
+// sequence: t = clamp((l(t) - l(t-1)) / (l(t-1) - l(t-2)), lo, hi), 0 when
+// the previous step did not move it
+__global__ void k_ws_shift_target(const double *w2, const double *w1, const double *w, double lo, double hi,
+                                  float *t) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double d = w1[0] - w2[0];
+  const double c = (fabs(d) > 0.0) ? (w[0] - w1[0]) / d : 0.0;
+  t[0] = (float)fmin(fmax(c, lo), hi);
+}
+
+// shift = l(t-1) + clamp(c, lo, hi) (l(t-1) - l(t-2)) - frac (l_s(t-1) - l(t-1)) / s
+// (c = 0 without a coefficient): below the predicted smallest eigenvalue by a
+// fraction of the mean spacing of the wanted ones
+__global__ void k_ws_shift(int s, const double *w2, const double *w1, const float *coef, double lo, double hi,
+                           double frac, double *shift) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double c = coef ? fmin(fmax((double)coef[0], lo), hi) : 0.0;
+  const double step = w2 ? w1[0] - w2[0] : 0.0;
+  shift[0] = w1[0] + c * step - frac * (w1[s - 1] - w1[0]) / (double)s;
+}
+
 // Features of the problem at step t for the next one: with g the mean
 // spacing of theta(t) (s ascending Ritz values), f_j = (theta_j(t) -
 // theta_s(t)) / g, f_{s+j} = (theta_j(t) - theta_j(t-1)) / g, f_{2s} =
@@ -551,6 +573,30 @@ int gsyeig_ws_extrapolate(int64_t n, int64_t s, const double *X, int64_t ldx, co
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   k_ws_extrapolate<<<dim3((unsigned)std::min<int64_t>(ceil_div(n, 256), 64), (unsigned)s), 256, 0, st>>>(
       n, (int)s, X, ldx, D, ldd, coef, lo, hi, out, ldo);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int gsyeig_ws_shift_target(const double *w_prev2, const double *w_prev, const double *w, double lo, double hi,
+                           float *target, void *stream) {
+  if (!w_prev2 || !w_prev || !w) return -1;
+  if (!target) return -6;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_ws_shift_target<<<1, 32, 0, st>>>(w_prev2, w_prev, w, lo, hi, target);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int gsyeig_ws_shift(int64_t s, const double *w_prev2, const double *w_prev, const float *coef, double lo, double hi,
+                    double frac, double *shift, void *stream) {
+  if (s < 2 || s > 4096) return -1;
+  if (!w_prev) return -3;
+  if (!shift) return -8;
+  if (coef && !w_prev2) return -2;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_ws_shift<<<1, 32, 0, st>>>((int)s, w_prev2, w_prev, coef, lo, hi, frac, shift);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;

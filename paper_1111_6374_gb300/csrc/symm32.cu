@@ -114,8 +114,14 @@ __global__ void __launch_bounds__(S32_THREADS) k_symm32(int NT, const float *__r
   __shared__ __align__(16) float tile[2][TS * TS];
   __shared__ __align__(16) float wj[2][TS * NB];
   const int i = blockIdx.x;
-  const int t = threadIdx.x, r = t % TS, q = t / TS;  // 4 column quads
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  // thread (row r, quarter kq of the tile's 64 k): all 16 vectors of row r
+  // over k = 16 kq .. 16 kq + 15; the W row of each k is one broadcast
+  // 64-byte read per warp, so a warp does 16 FMAs per 5 shared-memory
+  // wavefronts; the four quarters are summed once at the end
+  const int t = threadIdx.x, r = t % TS, kq = t / TS;
+  float acc[NB];
+#pragma unroll
+  for (int c = 0; c < NB; c++) acc[c] = 0.f;
   s32_prefetch(i, 0, T, W, tile[0], wj[0]);
   for (int step = 0; step < NT; step++) {
     const int b = step & 1;
@@ -128,33 +134,42 @@ __global__ void __launch_bounds__(S32_THREADS) k_symm32(int NT, const float *__r
     __syncthreads();  // every thread's copies of this step have landed
     const float *tl = tile[b];
     const float4 *wv = reinterpret_cast<const float4 *>(wj[b]);
-    if (step <= i) {
-      // Z_i(r, 4q..4q+3) += sum_k C_ij(r, k) W_j(k, 4q..4q+3); a warp's lanes
-      // read 32 rows of one column: distinct banks under the swizzle
-#pragma unroll 8
-      for (int k = 0; k < TS; k++) {
-        const float c = tl[(r ^ (k & 31)) + TS * k];
-        const float4 w = wv[k * (NB / 4) + q];
-        acc.x = fmaf(c, w.x, acc.x);
-        acc.y = fmaf(c, w.y, acc.y);
-        acc.z = fmaf(c, w.z, acc.z);
-        acc.w = fmaf(c, w.w, acc.w);
-      }
-    } else {
-      // Z_i(r, .) += sum_k C_ji(k, r) W_j(k, .): column r of the stored tile
-#pragma unroll 8
-      for (int k = 0; k < TS; k++) {
-        const float c = tl[(k ^ (r & 31)) + TS * r];
-        const float4 w = wv[k * (NB / 4) + q];
-        acc.x = fmaf(c, w.x, acc.x);
-        acc.y = fmaf(c, w.y, acc.y);
-        acc.z = fmaf(c, w.z, acc.z);
-        acc.w = fmaf(c, w.w, acc.w);
-      }
+    const bool row = step <= i;
+#pragma unroll 4
+    for (int kk = 0; kk < 16; kk++) {
+      const int k = 16 * kq + kk;
+      // row tiles: C_ij(r, k); column tiles: C_ji(k, r) (column r of the stored tile)
+      const float c = row ? tl[(r ^ (k & 31)) + TS * k] : tl[(k ^ (r & 31)) + TS * r];
+      const float4 w0 = wv[k * 4 + 0], w1 = wv[k * 4 + 1], w2 = wv[k * 4 + 2], w3 = wv[k * 4 + 3];
+      acc[0] = fmaf(c, w0.x, acc[0]);
+      acc[1] = fmaf(c, w0.y, acc[1]);
+      acc[2] = fmaf(c, w0.z, acc[2]);
+      acc[3] = fmaf(c, w0.w, acc[3]);
+      acc[4] = fmaf(c, w1.x, acc[4]);
+      acc[5] = fmaf(c, w1.y, acc[5]);
+      acc[6] = fmaf(c, w1.z, acc[6]);
+      acc[7] = fmaf(c, w1.w, acc[7]);
+      acc[8] = fmaf(c, w2.x, acc[8]);
+      acc[9] = fmaf(c, w2.y, acc[9]);
+      acc[10] = fmaf(c, w2.z, acc[10]);
+      acc[11] = fmaf(c, w2.w, acc[11]);
+      acc[12] = fmaf(c, w3.x, acc[12]);
+      acc[13] = fmaf(c, w3.y, acc[13]);
+      acc[14] = fmaf(c, w3.z, acc[14]);
+      acc[15] = fmaf(c, w3.w, acc[15]);
     }
     __syncthreads();  // buffer b is free for the copies of step + 2
   }
-  reinterpret_cast<float4 *>(Z + ((int64_t)i * TS + r) * NB)[q] = acc;
+  // sum the four quarters (tile[0] as scratch: 4 x 64 x 16 floats)
+  float *red = tile[0];
+#pragma unroll
+  for (int c = 0; c < NB; c++) red[(kq * TS + r) * NB + c] = acc[c];
+  __syncthreads();
+  for (int idx = t; idx < TS * NB; idx += S32_THREADS) {
+    const int rr = idx / NB, c = idx % NB;
+    Z[((int64_t)i * TS + rr) * NB + c] = ((red[(0 * TS + rr) * NB + c] + red[(1 * TS + rr) * NB + c]) +
+                                          red[(2 * TS + rr) * NB + c]) + red[(3 * TS + rr) * NB + c];
+  }
 }
 
 }  // namespace

@@ -106,12 +106,20 @@ class SequenceSolver:
       the coefficients c_j predicted from the previous two problems'
       eigenvalues and overlaps.
 
-    Every method runs the same Lanczos iteration with Ritz tests every
-    ``check_every`` steps, so a start vector rich in the wanted eigenvectors
-    stops early.  The solver's residual test decides acceptance in every
-    case."""
+    The two warm methods also set the shift of the next solve
+    (``gsyeig_opts.shift``): half a mean spacing of the wanted eigenvalues
+    below the previous smallest one (reuse), or below its extrapolation by a
+    coefficient the network predicts as its last output (learned).  With
+    A - shift B positive definite the solve takes the inverse route of
+    Section 3.1 even when A itself is indefinite (as the sequence's A(t)
+    become once an eigenvalue crosses zero); otherwise it falls back to the
+    direct route.  Every method runs the same Lanczos iteration with Ritz
+    tests every ``check_every`` steps, so a start vector rich in the wanted
+    eigenvectors stops early.  The solver's residual test decides acceptance
+    in every case."""
 
     C_LO, C_HI = 0.0, 1.5  # range of the extrapolation coefficients
+    SHIFT_FRAC = 0.5       # margin of the shift below the smallest eigenvalue, in mean spacings
 
     def __init__(self, s: int, method: str, B: torch.Tensor, mlp: Mlp | None = None, device=0, check_every: int = 16,
                  **opts):
@@ -129,6 +137,7 @@ class SequenceSolver:
         self.D = colmajor_empty(n, s, device=dev)
         self.start = colmajor_empty(n, s, device=dev)
         self.weights = torch.ones(s, device=dev, dtype=torch.float64)
+        self.sigma = torch.zeros(1, device=dev, dtype=torch.float64)
 
     def _st(self):
         return _stream(self.dev)
@@ -161,6 +170,13 @@ class SequenceSolver:
         self.align(X, X_prev, self.D, match=f[2 * s + 1:])
         return f
 
+    def shift_target(self, w_prev, w, w_next, out):
+        """The extrapolation coefficient of the smallest eigenvalue (gsyeig_ws_shift_target)."""
+        st = self.lib.gsyeig_ws_shift_target(_p(w_prev), _p(w), _p(w_next), self.C_LO, self.C_HI, _p(out), self._st())
+        if st != 0:
+            raise GsyeigError(st, "ws_shift_target")
+        return out
+
     def targets(self, X_prev, X, X_next, out):
         """B-optimal extrapolation coefficients of x_j(t) (gsyeig_ws_coef_targets)."""
         n, s = X.shape
@@ -177,7 +193,8 @@ class SequenceSolver:
     def solve(self, A: torch.Tensor, B: torch.Tensor):
         """One solve of the sequence (A, B not modified): (w, X, info, ms)."""
         s, sol = self.s, self.solver
-        opts = dict(start_block=None, start_weights=None)
+        opts = dict(start_block=None, start_weights=None, shift=0.0)
+        coef = None
         if self.method != "random" and self.prev:
             opts.update(start_block=self.prev[-1][1], start_weights=self.weights)
         if self.method == "learned" and len(self.prev) >= 2:
@@ -190,6 +207,15 @@ class SequenceSolver:
             if st != 0:
                 raise GsyeigError(st, "ws_extrapolate")
             opts.update(start_block=self.start, start_weights=self.weights)
+            coef = c[0, s:]
+        if self.method != "random" and self.prev:
+            w1 = self.prev[-1][0]
+            w0 = self.prev[-2][0] if len(self.prev) >= 2 else None
+            st = self.lib.gsyeig_ws_shift(s, _p(w0 if coef is not None else None), _p(w1), _p(coef), self.C_LO,
+                                          self.C_HI, self.SHIFT_FRAC, _p(self.sigma), self._st())
+            if st != 0:
+                raise GsyeigError(st, "ws_shift")
+            opts.update(shift=float(self.sigma.item()))
         sol.set_options(**opts)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -204,9 +230,10 @@ def evaluate_sequence(pencil, B, n: int, s: int, T: int, T_train: int, iters: in
                       check=None, device=0, seed: int = 0):
     """The warm-start experiment on a sequence: ``pencil(k)`` returns
     (A_k, B, lam_k).  Problems 0..T_train-1 are solved with the plain random
-    start; the network is trained on them (features of t, B-optimal
-    extrapolation coefficients from t-1, t, t+1); problems T_train..T-1 are
-    then solved by the three methods, each from its own previous solutions.
+    start; the network is trained on them (features of t; targets from t-1,
+    t, t+1: the B-optimal extrapolation coefficients of the eigenvectors and
+    the one of the smallest eigenvalue); problems T_train..T-1 are then
+    solved by the three methods, each from its own previous solutions.
     ``check(A, B, w, X, lam)`` (optional; lam the whole constructed spectrum,
     ascending) is called on every solution.
     Returns (totals {method: [operator applications, ms, restarts]},
@@ -224,10 +251,12 @@ def evaluate_sequence(pencil, B, n: int, s: int, T: int, T_train: int, iters: in
     feats, targs = [], []
     for k in range(1, T_train - 1):
         feats.append(collect.features(sols[k][0], sols[k - 1][0], sols[k][1], sols[k - 1][1]).clone())
-        targs.append(collect.targets(sols[k - 1][1], sols[k][1], sols[k + 1][1],
-                                     torch.empty(s, device=dev, dtype=torch.float32)).clone())
+        tk = torch.empty(s + 1, device=dev, dtype=torch.float32)
+        collect.targets(sols[k - 1][1], sols[k][1], sols[k + 1][1], tk[:s])
+        collect.shift_target(sols[k - 1][0], sols[k][0], sols[k + 1][0], tk[s:])
+        targs.append(tk)
     Xf, Tf = torch.stack(feats), torch.stack(targs)
-    net = Mlp(3 * s + 1, s, seed=seed, device=dev)
+    net = Mlp(3 * s + 1, s + 1, seed=seed, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     hist = net.train(Xf, Tf, iters, lr=lr)

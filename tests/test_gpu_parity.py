@@ -221,6 +221,34 @@ def test_solve_inverse_fallback_after_outer_updates():
     _check_pairs(A, B, _np(w), _np(X), w_or, w_or, "fallback after outer updates")
 
 
+def test_solve_shifted_inverse_route_matches_oracle():
+    """opts.shift: with an indefinite A (one negative lambda) and a shift
+    below the smallest eigenvalue, A - shift B is positive definite and the
+    solve takes the inverse route (info.inverse = 1) with lambda = shift +
+    1/mu; with a shift above an eigenvalue the factorisation of A - shift B
+    fails, A is restored and the direct route returns the same pairs.  Both
+    match the oracle at the 1e-10 gates."""
+    from paper_1111_6374_gb300 import Solver
+
+    n, s = 700, 10
+    lam = np.sort(np.random.default_rng(23).uniform(0.0, 1000.0, n))
+    lam[0] = -3.0  # A indefinite: one negative eigenvalue
+    A, B, lam = (t.numpy() for t in inputs.make_pencil(n, seed=23, lam=lam))
+    w_or, X_or = oracle.gsyeig(A, B, s)
+    assert w_or[0] < 0
+    for shift, route in ((w_or[0] - 3.0, 1), (0.5 * (w_or[2] + w_or[3]), 0)):
+        w, X, info = Solver(0, inverse=1, shift=float(shift)).solve(torch.from_numpy(A).cuda(),
+                                                                     torch.from_numpy(B).cuda(), s)
+        assert info["inverse"] == route, (shift, info["inverse"])
+        w, X = _np(w), _np(X)
+        cn = np.abs(lam).max()
+        assert np.all(np.abs(w - w_or) <= 1e-10 * np.abs(w_or) + 1e-14 * cn), (shift, np.abs(w - w_or).max())
+        assert _checks.eta(A, B, w, X).max() <= 1e-10
+        assert _checks.b_orth_err(B, X) <= 1e-10
+        ang, lim = _checks.max_subspace_angle(B, X, X_or, w, lam, cn, 1e-12 * cn)
+        assert ang <= lim, (ang, lim)
+
+
 @pytest.mark.parametrize("inverse", [0, 1], ids=["direct", "inverse"])
 def test_solve_preserve_inputs_and_verify(inverse):
     """opts.preserve_inputs leaves device A and B bit for bit as they were;
