@@ -1,4 +1,4 @@
-"""Batches of independent problems (configs[3]'s form at test size):
+"""Batches of independent problems of uneven order (a smaller form of the 64-problem benchmark):
 gsyeig_solve_batched against the oracle and against one-by-one solves.
 
 Every problem of a batch of uneven orders meets the 1e-10 gates against

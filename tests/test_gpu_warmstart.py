@@ -1,4 +1,4 @@
-"""The learned warm start (configs[4]'s form at test size) on the GPU.
+"""The learned warm start for a sequence of related pencils, at test size, on the GPU.
 
 * The network's tensor-core forward and backward kernels against the CPU
   FP64 oracle (oracle/mlp.py, which rounds the same operands to bf16):
