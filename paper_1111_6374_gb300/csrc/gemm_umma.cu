@@ -445,6 +445,23 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
       // the exponents this thread needs: its row's, and lane j < 16 holds column gjb + j's
       const int er_pre = (gi < g.M) ? ea[gi] : EXP_NONE;
       const int ec_pre = (lane < EPI_COLS && gjb + lane < g.N) ? eb[gjb + lane] : EXP_NONE;
+      const bool row_ok = gi < g.M;  // (no early exit: the warp shuffles below need every lane)
+      const int er = er_pre;
+      // which of this thread's elements it writes (bit c), and their column exponents
+      uint32_t okm = 0;
+      int ecv[EPI_COLS];
+#pragma unroll
+      for (int c = 0; c < EPI_COLS; c++) {
+        const int64_t gj = gjb + c, dd = gi - gj + g.diag;
+        const bool ok = row_ok && (gj < g.N) && !(g.mode == TRI_LOWER && dd < 0) && !(g.mode == TRI_UPPER && dd > 0);
+        const int ecs = __shfl_sync(0xffffffffu, ec_pre, c);
+        ecv[c] = ok ? ecs : EXP_NONE;
+        okm |= ok ? (1u << c) : 0u;
+      }
+      // the solver's updates (C += +-2^k A B) read C: its lines are brought
+      // into L2 while the tile's last K chunk is still in the tensor cores
+      // (a prefetch holds no registers: 18 warps leave at most 96 per thread)
+      const bool prefetch = alpha_pow2 && beta_mode == 1;
       // V = sum over chunks of the recombined level sums, a signed 128-bit
       // integer (vh:vl) per element, held in registers
       int32_t vh[EPI_COLS];
@@ -455,6 +472,11 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         vl[c] = 0;
       }
       for (int64_t ch = 0; ch < nch; ch++, fc++) {
+        if (prefetch && ch == nch - 1) {
+#pragma unroll
+          for (int c = 0; c < EPI_COLS; c++)
+            if ((okm >> c) & 1) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(C + gi + (gjb + c) * ldc));
+        }
         // the warp decides together (the TMEM loads and shuffles below are
         // .sync.aligned: no lane may leave on its own)
         const int set = (int)(fc & 1);
@@ -493,19 +515,6 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sptr(&acc_empty[set])) : "memory");
       }
       if (!ok) break;
-      const bool row_ok = gi < g.M;  // (no early exit: the warp shuffles below need every lane)
-      const int er = er_pre;
-      // which of this thread's 16 elements it writes (bit c), and their column exponents
-      uint32_t okm = 0;
-      int ecv[EPI_COLS];
-#pragma unroll
-      for (int c = 0; c < EPI_COLS; c++) {
-        const int64_t gj = gjb + c, dd = gi - gj + g.diag;
-        const bool ok = row_ok && (gj < g.N) && !(g.mode == TRI_LOWER && dd < 0) && !(g.mode == TRI_UPPER && dd > 0);
-        const int ecs = __shfl_sync(0xffffffffu, ec_pre, c);
-        ecv[c] = ok ? ecs : EXP_NONE;
-        okm |= ok ? (1u << c) : 0u;
-      }
       if (alpha_pow2 && beta_mode != 2) {
         // the solver's updates, C = +-2^k A B (+ C): V rounded to FP64 first
         // (branch-free; the 128-bit accumulators die here), then every load
