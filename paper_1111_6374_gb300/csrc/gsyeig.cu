@@ -1406,12 +1406,19 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     double *d1 = a_first ? dA : dB, *d2 = a_first ? dB : dA;
     const double *s1 = a_first ? A : B, *s2 = a_first ? B : A;
     const int64_t l1 = a_first ? lda : ldb, l2 = a_first ? ldb : lda;
-    GS_CUDA(cudaMemcpy2DAsync(d1, n * sizeof(double), s1, l1 * sizeof(double), n * sizeof(double), n,
-                              cudaMemcpyHostToDevice, st));
+    // (a matrix stored with ld = n is one contiguous block: one linear copy)
+    auto h2d = [&](double *d, const double *src, int64_t ld, cudaStream_t s) -> int {
+      if (ld == n)
+        GS_CUDA(cudaMemcpyAsync(d, src, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice, s));
+      else
+        GS_CUDA(cudaMemcpy2DAsync(d, n * sizeof(double), src, ld * sizeof(double), n * sizeof(double), n,
+                                  cudaMemcpyHostToDevice, s));
+      return GSYEIG_SUCCESS;
+    };
+    GS_TRY(h2d(d1, s1, l1, st));
     GS_CUDA(cudaEventRecord(h->cp_first, st));
     GS_CUDA(cudaStreamWaitEvent(h->cp, h->cp_first, 0));
-    GS_CUDA(cudaMemcpy2DAsync(d2, n * sizeof(double), s2, l2 * sizeof(double), n * sizeof(double), n,
-                              cudaMemcpyHostToDevice, h->cp));
+    GS_TRY(h2d(d2, s2, l2, h->cp));
     GS_CUDA(cudaEventRecord(h->cp_ev, h->cp));
     copy_pending.st = h->cp;
   }

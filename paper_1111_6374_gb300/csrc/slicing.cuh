@@ -192,18 +192,30 @@ __global__ void k_split2(int64_t M, int64_t N, int64_t K, int64_t Mpad, int64_t 
     if (kcontig) tile[j][tx] = v; else tile[tx][j] = v;
   }
   __syncthreads();
-  for (int j = ty; j < 32; j += 8) {
-    const int64_t r = r0 + j, k = k0 + tx;
-    if (r >= Rpad || k >= Kpad) continue;
-    const double v = tile[j][tx];
-    const int e = rowe[j];
+  // digits: thread u < 128 takes row j = u / 4 and the 8 consecutive k of
+  // group u % 4, so that the 8 digits of one slice (contiguous in both
+  // layouts, 16-byte aligned since Kpad is a multiple of 32) leave as one
+  // 16-byte store; all tests on the values are integer ones
+  const int u = ty * 32 + tx;
+  if (u >= 128) return;
+  const int j = u >> 2, q = u & 3;
+  const int64_t r = r0 + j, kb = k0 + 8 * q;
+  if (r >= Rpad || kb >= Kpad) return;
+  const int e = rowe[j];
+  uint32_t packed[S][4];
+#pragma unroll
+  for (int p = 0; p < S; p++)
+#pragma unroll
+    for (int w = 0; w < 4; w++) packed[p][w] = 0u;
+#pragma unroll
+  for (int kk = 0; kk < 8; kk++) {
+    const int64_t k = kb + kk;
+    const uint64_t ub = (uint64_t)__double_as_longlong(tile[j][8 * q + kk]);
     uint64_t Xm = 0;
-    bool neg = false;
-    if (v != 0.0 && e != EXP_NONE) {
-      const uint64_t u = (uint64_t)__double_as_longlong(v);
-      neg = (u >> 63) != 0;
-      const int E = (int)((u >> 52) & 0x7FF);
-      uint64_t m = u & ((1ull << 52) - 1);
+    const bool neg = (ub >> 63) != 0;
+    if ((ub << 1) != 0 && e != EXP_NONE) {  // v != 0
+      const int E = (int)((ub >> 52) & 0x7FF);
+      uint64_t m = ub & ((1ull << 52) - 1);
       int Eeff = E;
       if (E != 0) m |= (1ull << 52); else Eeff = 1;
       const int ks = (kA && k < K) ? sgn * kshift_of(kA, kB, k) : 0;
@@ -227,9 +239,14 @@ __global__ void k_split2(int64_t M, int64_t N, int64_t K, int64_t Mpad, int64_t 
 #pragma unroll
     for (int p = 0; p < S; p++) {
       const int d = neg ? -dg[p] : dg[p];
-      *reinterpret_cast<__nv_bfloat16 *>(dst + digit_off(L, p, r, k, Rpad, Kpad)) = __float2bfloat16_rn((float)d);
+      const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)d));
+      packed[p][kk >> 1] |= bits << (16 * (kk & 1));
     }
   }
+#pragma unroll
+  for (int p = 0; p < S; p++)
+    *reinterpret_cast<uint4 *>(dst + digit_off(L, p, r, kb, Rpad, Kpad)) =
+        make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
 }
 
 // Host side: digits and exponents of op(A) (M x K) and op(B) (rows = its N
