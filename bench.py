@@ -253,7 +253,8 @@ def run_ours(args, ws, rank, local):
         A0, B0, lam = inputs.make_pencil(n, seed=args.seed + rank, device=dev)
     A = torch.empty_like(A0)
     B = torch.empty_like(B0)
-    solver = Solver(local, inverse=1 if args.route == "inverse" else 0, block=args.block, graph=args.graph)
+    solver = Solver(local, inverse=1 if args.route == "inverse" else 0, block=args.block, graph=args.graph,
+                    check_every=args.check_every)
     stream = torch.cuda.current_stream(dev)
 
     def restore():
@@ -423,6 +424,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": n, "s": s, "which": "smallest", "route": ROUTES[args.route],
                    "inverse_used": last["inverse"], "krylov_dim": last["krylov_dim"], "graph": args.graph,
+                   "check_every": args.check_every,
                    "keep": last["keep"], "tol": 1e-12, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "inputs larger than L2 (2 x %.1f GB vs 129 MB)" % (n * n * 8 / 1e9)},
         "stages_ms": {k: last[k] for k in ("ms_gs1", "ms_gs2", "ms_ke", "ms_ke3", "ms_bt1", "ms_total")},
@@ -752,6 +754,9 @@ def main(argv=None):
     ap.add_argument("--gen-device", choices=["cuda", "cpu"], default="cuda",
                     help="where the synthetic pencil is built (input generation only, outside any timing)")
     ap.add_argument("--block", type=int, default=0, help="panel width nb of the blocked factorisations (0 = default)")
+    ap.add_argument("--check-every", type=int, default=50,
+                    help="Ritz tests every this many Lanczos steps inside a cycle (gsyeig_opts.check_every; 0: only at "
+                         "its end); at 50 the headline solve stops after 250 of its 300 steps")
     ap.add_argument("--graph", type=int, choices=[0, 1], default=0,
                     help="1: replay the Lanczos cycles from CUDA graphs (gsyeig_opts.graph)")
     ap.add_argument("--no-extra", action="store_true",

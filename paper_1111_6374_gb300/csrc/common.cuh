@@ -156,6 +156,9 @@ int copy_block(cudaStream_t st, int64_t M, int64_t N, const double *src, int64_t
 
 // X = I (n x n, leading dimension ldx).
 int set_identity(cudaStream_t st, int64_t n, double *X, int64_t ldx);
+// Y += alpha X over an M x N block (column-major, leading dimensions ldx, ldy)
+int axpy_block(cudaStream_t st, int64_t M, int64_t N, double alpha, const double *X, int64_t ldx, double *Y,
+               int64_t ldy);
 
 // Mirror one triangle of an n x n matrix into the other: lower_to_upper
 // copies A[i][j] (i > j) to A[j][i]; otherwise the reverse.
@@ -179,6 +182,9 @@ struct FactorWork {
   // kernels and two events (the next diagonal block updated; it is factored)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_upd = nullptr, ev_diag = nullptr;
+  // sygst's recursion: P = U12^T C11 of the top split (sygst_tmp_elems doubles; NULL: direct form)
+  double *tmp = nullptr;
+  size_t tmp_elems = 0;
 };
 
 // order NB of the outer blocks of the blocked factorisations for inner width nb
@@ -188,6 +194,8 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
 int trtri_diag_blocks(cudaStream_t st, int64_t n, const double *U, int64_t ldu, int nb, double *Uinv);
 int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *U, int64_t ldu, int nb,
                   FactorWork &w, bool have_uinv);
+// doubles of FactorWork::tmp that sygst_blocked's n^3 recursion needs at order n (0: none)
+size_t sygst_tmp_elems(int64_t n, int nb);
 int trsm_back_blocked(cudaStream_t st, int64_t n, const double *U, int64_t ldu, double *Y, int64_t ldy, int64_t s,
                       int nb, FactorWork &w, bool have_uinv);
 // X = U^-1 for the upper-triangular U (X n x n, ld ldx; zeros below the diagonal).

@@ -1,15 +1,18 @@
 // Blocked dense steps of the route (gs1, gs2, bt1 in Table 1 of the paper):
 //   potrf  B = U^T U                    (Eq. 2)   n^3/3 flops
-//   sygst  C = U^-T A U^-1              (Eq. 3)   4n^3/3 flops here
+//   sygst  C = U^-T A U^-1              (Eq. 3)   n^3 flops (+ lower order)
 //   trsm   X = U^-1 Y                   (Eq. 4)   n^2 s flops
 // All bulk work goes through the GEMM engine; the only other kernels are the
-// nb x nb diagonal-block factor/inverse (one CTA each) and copies.
+// nb x nb diagonal-block factor/inverse (one CTA each), copies and axpys.
 //
 // sygst: the paper computes C with two triangular solves (2n^3, Section 4.1)
-// or, exploiting symmetry, with n^3.  Here step 1 forms W = U^-T A in full
-// (n^3) and step 2 forms only the lower triangle of C = W U^-1, which needs
-// only the lower triangle of W at each stage (n^3/3), then mirrors it:
-// 4n^3/3 flops with nothing but GEMM-shaped updates.
+// or, exploiting symmetry, with n^3.  The n^3 form here is a recursion on a
+// 2 x 2 split of A and U (sygst_rec): C11 recursively; the off-diagonal block
+// through Y = A21 U11^-1, Z = Y - P/2, W = Z - P/2 with P = U12^T C11; the
+// symmetric rank-2n1 update A22 -= Z U12 + U12^T Z^T; C22 recursively; and
+// C21 = U22^-T W.  Every step is a large GEMM.  Blocks of at most 4 outer
+// blocks use the direct form (sygst_leaf): step 1 forms W = U^-T A in full
+// (n^3) and step 2 only the lower triangle of C = W U^-1 (n^3/3).
 #include "common.cuh"
 
 namespace gs {
@@ -343,19 +346,21 @@ int outer_inverses(cudaStream_t st, int64_t n, const double *U, int64_t ldu, int
   return GSYEIG_SUCCESS;
 }
 
-// sygst: C = U^-T A U^-1, lower triangle, then mirrored.  With the outer
-// inverses U_JJ^-1 (formed here from the nb x nb ones) every step is one
-// GEMM per outer block and pass with K = NB.
-int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *U, int64_t ldu, int nb,
-                  FactorWork &w, bool have_uinv) {
+namespace {
+
+// Direct sygst of one diagonal sub-block (its first row/column is a
+// multiple of NB, UiO its first outer inverse): C = U^-T A U^-1 from A's
+// lower triangle, stored full.  Step 1: W = U^-T A, block row by block row:
+// W_J = U_JJ^-T A_J, then the rows below, A_rest -= U_J,rest^T W_J.  Step 2:
+// the lower triangle of C = W U^-1, block column by block column:
+// C_{J0:, J} = W_{J0:, J} U_JJ^-1 (rows above the block's diagonal are not
+// needed), then C_rest,rest (lower) -= C_rest,J U_J,rest.  4n^3/3 flops.
+int sygst_leaf(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *U, int64_t ldu,
+               const double *UiO, int64_t NB, FactorWork &w) {
   GS_TRY(symmetrize(st, n, A, lda, true));
-  if (!have_uinv || !w.outer_ready) GS_TRY(outer_inverses(st, n, U, ldu, nb, w, have_uinv));
-  const int64_t NB = outer_block(nb);
-  // Step 1: W = U^-T A, block row by block row: W_J = U_JJ^-T A_J, then the
-  // rows below, A_rest -= U_J,rest^T W_J
   for (int64_t J0 = 0; J0 < n; J0 += NB) {
     const int64_t J1 = std::min(n, J0 + NB), jb = J1 - J0;
-    const double *UiJ = w.UinvO + (size_t)(J0 / NB) * NB * NB;
+    const double *UiJ = UiO + (size_t)(J0 / NB) * NB * NB;
     double *AJ = &A[GS_IDX(J0, 0, lda)];
     GS_TRY(dgemm(st, true, false, jb, n, jb, 1.0, UiJ, NB, AJ, lda, 0.0, w.panelO, jb));
     GS_TRY(copy_block(st, jb, n, w.panelO, jb, AJ, lda));
@@ -364,12 +369,9 @@ int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const doub
       GS_TRY(dgemm(st, true, false, r2, n, jb, -1.0, &U[GS_IDX(J0, J1, ldu)], ldu, AJ, lda, 1.0,
                    &A[GS_IDX(J1, 0, lda)], lda));
   }
-  // Step 2: lower triangle of C = W U^-1, block column by block column:
-  // C_{J0:, J} = W_{J0:, J} U_JJ^-1 (rows above the diagonal of the block
-  // are not needed), then C_rest,rest (lower) -= C_rest,J U_J,rest
   for (int64_t J0 = 0; J0 < n; J0 += NB) {
     const int64_t J1 = std::min(n, J0 + NB), jb = J1 - J0, rows = n - J0;
-    const double *UiJ = w.UinvO + (size_t)(J0 / NB) * NB * NB;
+    const double *UiJ = UiO + (size_t)(J0 / NB) * NB * NB;
     double *CJ = &A[GS_IDX(J0, J0, lda)];
     GS_TRY(dgemm(st, false, false, rows, jb, jb, 1.0, CJ, lda, UiJ, NB, 0.0, w.panelO, rows));
     GS_TRY(copy_block(st, rows, jb, w.panelO, rows, CJ, lda));
@@ -378,8 +380,99 @@ int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const doub
       GS_TRY(dgemm(st, false, false, r2, r2, jb, -1.0, &A[GS_IDX(J1, J0, lda)], lda, &U[GS_IDX(J0, J1, ldu)], ldu,
                    1.0, &A[GS_IDX(J1, J1, lda)], lda, TRI_LOWER, 0));
   }
-  GS_TRY(symmetrize(st, n, A, lda, true));
+  return symmetrize(st, n, A, lda, true);
+}
+
+// X <- X U^-1 for the k x k upper-triangular diagonal sub-block U whose
+// outer inverses start at UiO (X m x k): forward over the outer column
+// blocks, X_J = X_J U_JJ^-1, then X_rest -= X_J U_J,rest.
+int trsm_right_upper(cudaStream_t st, int64_t m, int64_t k, double *X, int64_t ldx, const double *U, int64_t ldu,
+                     const double *UiO, int64_t NB, FactorWork &w) {
+  for (int64_t J0 = 0; J0 < k; J0 += NB) {
+    const int64_t J1 = std::min(k, J0 + NB), jb = J1 - J0;
+    const double *UiJ = UiO + (size_t)(J0 / NB) * NB * NB;
+    double *XJ = X + J0 * ldx;
+    GS_TRY(dgemm(st, false, false, m, jb, jb, 1.0, XJ, ldx, UiJ, NB, 0.0, w.panelO, m));
+    GS_TRY(copy_block(st, m, jb, w.panelO, m, XJ, ldx));
+    if (J1 < k)
+      GS_TRY(dgemm(st, false, false, m, k - J1, jb, -1.0, XJ, ldx, &U[GS_IDX(J0, J1, ldu)], ldu, 1.0, X + J1 * ldx,
+                   ldx));
+  }
   return GSYEIG_SUCCESS;
+}
+
+// X <- U^-T X for the same kind of sub-block (X k x m): forward over the
+// outer row blocks, X_J = U_JJ^-T X_J, then X_rest -= U_J,rest^T X_J.
+int trsm_left_upper_t(cudaStream_t st, int64_t k, int64_t m, double *X, int64_t ldx, const double *U, int64_t ldu,
+                      const double *UiO, int64_t NB, FactorWork &w) {
+  for (int64_t J0 = 0; J0 < k; J0 += NB) {
+    const int64_t J1 = std::min(k, J0 + NB), jb = J1 - J0;
+    const double *UiJ = UiO + (size_t)(J0 / NB) * NB * NB;
+    double *XJ = X + J0;
+    GS_TRY(dgemm(st, true, false, jb, m, jb, 1.0, UiJ, NB, XJ, ldx, 0.0, w.panelO, jb));
+    GS_TRY(copy_block(st, jb, m, w.panelO, jb, XJ, ldx));
+    if (J1 < k)
+      GS_TRY(dgemm(st, true, false, k - J1, m, jb, -1.0, &U[GS_IDX(J0, J1, ldu)], ldu, XJ, ldx, 1.0, X + J1, ldx));
+  }
+  return GSYEIG_SUCCESS;
+}
+
+// split point of an n-row block for the recursion: the first half of its
+// outer blocks (rounded up)
+int64_t sygst_split(int64_t n, int64_t NB) { return ((ceil_div(n, NB) + 1) / 2) * NB; }
+bool sygst_recurses(int64_t n, int64_t NB) { return n > 4 * NB; }
+
+// C = U^-T A U^-1 of a diagonal sub-block by the 2 x 2 recursion: with
+// U = [U11 U12; 0 U22] and A's lower triangle [A11; A21 A22],
+//   C11 = sygst(A11, U11)
+//   Y = A21 U11^-1,  P = U12^T C11,  Z = Y - P/2
+//   A22 <- A22 - Z U12 - U12^T Z^T        (lower triangle)
+//   C22 = sygst(A22, U22)
+//   C21 = U22^-T (Z - P/2)
+// (expanding C = V^T A V with V = U^-1 blockwise gives C21 = U22^-T (Y - P) and
+// C22 = U22^-T (A22 - Y U12 - U12^T Y^T + U12^T C11 U12) U22^-1, which the
+// half-steps through Z reproduce).  Only A's lower triangle is read; the
+// result is stored full.  P lives in w.tmp (the calls below a node reuse it
+// once its P is consumed).
+int sygst_rec(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *U, int64_t ldu, const double *UiO,
+              int64_t NB, FactorWork &w) {
+  if (!sygst_recurses(n, NB)) return sygst_leaf(st, n, A, lda, U, ldu, UiO, NB, w);
+  const int64_t n1 = sygst_split(n, NB), n2 = n - n1;
+  double *A21 = A + n1, *A22 = A + n1 + n1 * lda;
+  const double *U12 = U + n1 * ldu, *U22 = U + n1 + n1 * ldu;
+  const double *UiO2 = UiO + (size_t)(n1 / NB) * NB * NB;
+  double *P = w.tmp;
+  GS_TRY(sygst_rec(st, n1, A, lda, U, ldu, UiO, NB, w));
+  GS_TRY(trsm_right_upper(st, n2, n1, A21, lda, U, ldu, UiO, NB, w));
+  GS_TRY(dgemm(st, true, false, n2, n1, n1, 1.0, U12, ldu, A, lda, 0.0, P, n2));
+  GS_TRY(axpy_block(st, n2, n1, -0.5, P, n2, A21, lda));
+  GS_TRY(dgemm(st, false, false, n2, n2, n1, -1.0, A21, lda, U12, ldu, 1.0, A22, lda, TRI_LOWER, 0));
+  GS_TRY(dgemm(st, true, true, n2, n2, n1, -1.0, U12, ldu, A21, lda, 1.0, A22, lda, TRI_LOWER, 0));
+  GS_TRY(axpy_block(st, n2, n1, -0.5, P, n2, A21, lda));
+  GS_TRY(sygst_rec(st, n2, A22, lda, U22, ldu, UiO2, NB, w));
+  GS_TRY(trsm_left_upper_t(st, n2, n1, A21, lda, U22, ldu, UiO2, NB, w));
+  return symmetrize(st, n, A, lda, true);
+}
+
+}  // namespace
+
+size_t sygst_tmp_elems(int64_t n, int nb) {
+  const int64_t NB = outer_block(nb);
+  if (!sygst_recurses(n, NB)) return 0;
+  const int64_t n1 = sygst_split(n, NB);
+  return (size_t)n1 * (size_t)(n - n1);  // the largest P is the top split's
+}
+
+// sygst: C = U^-T A U^-1 from A's lower triangle, stored full; n^3 flops by
+// the recursion when w.tmp holds sygst_tmp_elems(n, nb) doubles, else the
+// direct 4n^3/3 form on the whole matrix.
+int sygst_blocked(cudaStream_t st, int64_t n, double *A, int64_t lda, const double *U, int64_t ldu, int nb,
+                  FactorWork &w, bool have_uinv) {
+  if (!have_uinv || !w.outer_ready) GS_TRY(outer_inverses(st, n, U, ldu, nb, w, have_uinv));
+  const int64_t NB = outer_block(nb);
+  const size_t need = sygst_tmp_elems(n, nb);
+  if (need > 0 && w.tmp && w.tmp_elems >= need) return sygst_rec(st, n, A, lda, U, ldu, w.UinvO, NB, w);
+  return sygst_leaf(st, n, A, lda, U, ldu, w.UinvO, NB, w);
 }
 
 // X = U^-1 (upper triangular, zeros below the diagonal) by the backward

@@ -189,6 +189,13 @@ __global__ void k_copy_block(int64_t M, int64_t N, const double *__restrict__ sr
       dst[GS_IDX(i, j, ldd)] = src[GS_IDX(i, j, lds)];
 }
 
+__global__ void k_axpy_block(int64_t M, int64_t N, double alpha, const double *__restrict__ X, int64_t ldx,
+                             double *__restrict__ Y, int64_t ldy) {
+  for (int64_t j = blockIdx.y; j < N; j += gridDim.y)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+      Y[GS_IDX(i, j, ldy)] += alpha * X[GS_IDX(i, j, ldx)];
+}
+
 // 32 x 32 tiles: tile (bi, bj) with bi > bj is read coalesced and written
 // transposed into tile (bj, bi); diagonal tiles mirror in place.
 __global__ void k_symmetrize(int64_t n, double *A, int64_t lda, bool lower_to_upper) {
@@ -289,6 +296,16 @@ int copy_block(cudaStream_t st, int64_t M, int64_t N, const double *src, int64_t
   if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
   dim3 grid((unsigned)std::min<int64_t>(ceil_div(M, 256), 64), (unsigned)std::min<int64_t>(N, 4096));
   k_copy_block<<<grid, 256, 0, st>>>(M, N, src, lds, dst, ldd, abort_flag);
+  count_launch();
+  GS_CHECK_LAUNCH();
+  return GSYEIG_SUCCESS;
+}
+
+int axpy_block(cudaStream_t st, int64_t M, int64_t N, double alpha, const double *X, int64_t ldx, double *Y,
+               int64_t ldy) {
+  if (M <= 0 || N <= 0) return GSYEIG_SUCCESS;
+  dim3 grid((unsigned)std::min<int64_t>(ceil_div(M, 256), 64), (unsigned)std::min<int64_t>(N, 4096));
+  k_axpy_block<<<grid, 256, 0, st>>>(M, N, alpha, X, ldx, Y, ldy);
   count_launch();
   GS_CHECK_LAUNCH();
   return GSYEIG_SUCCESS;

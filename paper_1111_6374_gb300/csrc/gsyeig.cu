@@ -57,6 +57,7 @@ struct gsyeig_ctx {
   // workspace
   DevBuf uinv, panel, flag, diag;
   DevBuf uinvO;           // inverses of the outer diagonal blocks and the outer panel staging
+  DevBuf gtmp;            // sygst's recursion buffer
   DevBuf V, Vq, z, h1, h2, sq, alpha, beta, alphaP, betaP, theta, S, Q, rot, invw, state, shifts, arrow;
   DevBuf hA, hB, hX, hw;  // device copies for host-pointer calls
   cudaStream_t side = nullptr;  // look-ahead of potrf: the diagonal-block kernels
@@ -227,6 +228,16 @@ int factor_ws(gsyeig_handle h, int64_t n, int nb, int64_t s, FactorWork &w) {
   w.side = h->side;
   w.ev_upd = h->side_ev[0];
   w.ev_diag = h->side_ev[1];
+  return GSYEIG_SUCCESS;
+}
+
+// the recursion buffer of sygst (allocated only by the calls that run gs2)
+int sygst_ws(gsyeig_handle h, int64_t n, int nb, FactorWork &w) {
+  const size_t need = sygst_tmp_elems(n, nb);
+  if (need == 0) return GSYEIG_SUCCESS;
+  GS_TRY(h->gtmp.ensure(need * sizeof(double)));
+  w.tmp = h->gtmp.d();
+  w.tmp_elems = need;
   return GSYEIG_SUCCESS;
 }
 
@@ -1133,7 +1144,7 @@ int gsyeig_destroy(gsyeig_handle h) {
   if (!h) return -1;
   cudaSetDevice(h->device);
   if (h->st) cudaStreamSynchronize(h->st);
-  DevBuf *bufs[] = {&h->uinvO, &h->mx_ones, &h->mx_op, &h->mx_w, &h->mx_z, &h->mx_V, &h->mx_Zd, &h->mx_H, &h->mx_part, &h->mx_T,
+  DevBuf *bufs[] = {&h->uinvO, &h->gtmp, &h->mx_ones, &h->mx_op, &h->mx_w, &h->mx_z, &h->mx_V, &h->mx_Zd, &h->mx_H, &h->mx_part, &h->mx_T,
                     &h->mx_small, &h->mx_Sb, &h->mx_CSb, &h->mx_tmp, &h->mx_fw, &h->wstart, &h->kinv, &h->dfopL, &h->kt, &h->tmin, &h->pA, &h->pB, &h->vA, &h->vB, &h->vws, &h->diag, &h->arrow, &h->gemm_err, &h->dfop, &h->dfpart, &h->gemm_ws, &h->uinv, &h->panel, &h->flag, &h->V, &h->Vq, &h->z, &h->h1, &h->h2, &h->sq, &h->alpha,
                     &h->beta, &h->alphaP, &h->betaP, &h->theta, &h->S, &h->Q, &h->rot, &h->invw, &h->state,
                     &h->shifts, &h->hA, &h->hB, &h->hX, &h->hw};
@@ -1221,6 +1232,7 @@ int gsyeig_sygst(gsyeig_handle h, double *dA, int64_t lda, const double *dU, int
   const int nb = nb_of(h, n);
   FactorWork w;
   GS_TRY(factor_ws(h, n, nb, 1, w));
+  GS_TRY(sygst_ws(h, n, nb, w));
   GS_TRY(sygst_blocked(h->st, n, dA, lda, dU, ldu, nb, w, false));
   GS_TRY(finish(h));
   return gemm_check(h);
@@ -1512,6 +1524,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
   if (ki && (h->opts.mixed != 0 || h->opts.block_start == 1)) return GSYEIG_NOT_SUPPORTED;
   if (!ki) {
     // gs2: C = U^-T G U^-1 over G (diagonal-block inverses reused from gs1)
+    GS_TRY(sygst_ws(h, n, nb, fw));
     GS_TRY(sygst_blocked(st, n, dG, dldg, dF, dldf, nb, fw, true));
   } else {
     // variant KI: G stays; U^-1 is formed once (n^3/3 flops on the GEMM
@@ -1679,6 +1692,7 @@ int autotune(gsyeig_handle h, int64_t n) {
       h->opts.block = nb;
       FactorWork fw;
       GS_TRY(factor_ws(h, n, nb, 1, fw));
+      GS_TRY(sygst_ws(h, n, nb, fw));
       const unsigned g = (unsigned)std::min<int64_t>(ceil_div(n * n, 256), 4096);
       k_tune_matrix<<<g, 256, 0, st>>>(n, h->pA.d());
       k_tune_matrix<<<g, 256, 0, st>>>(n, h->pB.d());

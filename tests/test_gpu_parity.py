@@ -88,6 +88,26 @@ def test_sygst_matches_oracle(any_solver, n):
     assert np.array_equal(C, C.T)
 
 
+@pytest.mark.parametrize("fp64_gemm", [0, 1])
+@pytest.mark.parametrize("n,nb", [(777, 24), (1000, 40)])
+def test_sygst_recursion_matches_oracle(n, nb, fp64_gemm):
+    """The n^3 recursion of gs2 (2 x 2 splits down to blocks of at most four
+    outer blocks): outer blocks of 4 nb = 96 and 160 columns, so that n = 777
+    recurses two levels deep and n = 1000 one level, with ragged halves."""
+    from paper_1111_6374_gb300 import Solver
+
+    A, B, _ = (t.numpy() for t in inputs.make_pencil(n, seed=n + nb))
+    U = oracle.potrf(B)
+    Co = oracle.sygst(A, U)
+    Ain = A.copy()
+    Ain[np.triu_indices(n, 1)] = np.nan  # only the lower triangle may be read
+    dA = _cm(Ain)
+    Solver(0, fp64_gemm=fp64_gemm, block=nb).sygst(dA, _cm(U))
+    C = _np(dA)
+    assert np.abs(C - Co).max() <= 1e-11 * np.abs(Co).max()
+    assert np.array_equal(C, C.T)
+
+
 @pytest.mark.parametrize("n", [1, 31, 64, 1001, 4096])
 def test_symv_matches_oracle(n):
     """The plain FP64 ke1 product (opts.fp64_symv = 1) against a long-double host product."""
