@@ -212,6 +212,11 @@ typedef struct {
   /* opts.profile = 1: launches and event time of the fp32 block operator of the mixed stage */
   int64_t symm32_launches;
   double symm32_ms;
+  /* host inputs: event time from the start of the call to the end of the first matrix's transfer
+   * (the other overlaps the Cholesky factorisation), and the host time the two copy requests took
+   * to return (near zero for page-locked buffers; a pageable buffer is copied through staging
+   * memory before the request returns) */
+  double ms_h2d_first, host_ms_h2d_enqueue;
 } gsyeig_info;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t

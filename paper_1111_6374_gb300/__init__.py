@@ -72,7 +72,7 @@ class Info(ctypes.Structure):
                [(f, ctypes.c_int64) for f in ("block_steps", "refine_iters")] + \
                [(f, ctypes.c_double) for f in ("ms_block_lanczos", "ms_refine")] + \
                [(f, ctypes.c_int64) for f in ("refine_stop", "refine_fallback", "symm32_launches")] + \
-               [("symm32_ms", ctypes.c_double)]
+               [(f, ctypes.c_double) for f in ("symm32_ms", "ms_h2d_first", "host_ms_h2d_enqueue")]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -18,8 +18,6 @@
 namespace gs {
 namespace {
 
-constexpr int DIAG_THREADS = 256;
-
 // Shared-memory nb x nb block, column-major with leading dimension nb + 1.
 struct SmemBlock {
   double *p;
@@ -27,83 +25,121 @@ struct SmemBlock {
   __device__ double &operator()(int i, int j) { return p[i + j * ld]; }
 };
 
-// 1/d to within an ulp for any positive finite d: d = f 2^k with f in
-// [1/2, 1) (frexp, exact), an FP32 seed of 1/f refined by two Newton steps
-// in FP64, then scaled back by 2^-k (ldexp, exact unless the result leaves
-// the FP64 range).  The reduction keeps the FP32 seed away from FP32's
-// overflow and subnormal ranges, which pivots of a pencil scaled by 2^+-140
-// reach.  GB300's FP64 divide is a long dependent sequence on a narrow pipe.
-__device__ __forceinline__ double recip(double d) {
-  int k;
-  const double f = frexp(d, &k);
-  double r = (double)(1.0f / (float)f);
-  double e = fma(-f, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-f, r, 1.0);
-  r = fma(r, e, r);
-  return ldexp(r, -k);
-}
+// The diagonal block B[k0:k0+kb, k0:k0+kb] (upper triangle) is factored in
+// place, B_kk = U_kk^T U_kk, by a right-looking Cholesky over sub-panels of
+// PW rows, three launches each: the PW x PW diagonal sub-block (one warp),
+// the sub-panel's rows right of it (U_pp^-T times the block row, one warp
+// per column, many CTAs) and the rank-PW update of the rest of the block
+// (16 x 16 tiles of its upper triangle, many CTAs).  GB300's FP64 pipe is
+// narrow, so the flops of the block (kb^3/3) are spread over several SMs;
+// only the sub-blocks' O(PW^3) stay on one warp.  1 / U(i, i) is left in
+// rdiag[0..kb).  A non-positive or NaN pivot records its global 1-based
+// index in *flag and stops; every later launch of the block (and every GEMM
+// given the flag) then returns at once.  Only the upper triangle of the
+// block is written.
+constexpr int PW = 32;
 
-// Factor the diagonal block B[k0:k0+kb, k0:k0+kb] (upper triangle) in
-// place, B_kk = U_kk^T U_kk, and leave 1 / U_kk(i, i) in rdiag[0..kb).
-// Right-looking on the unscaled rows, A'(r, c) = A(r, c) - A(j, r) A(j, c) /
-// A(j, j): each step needs one reciprocal (computed by every thread that
-// uses it, so no serial section), and the square roots are applied to all
-// rows at the end in parallel, U(j, c) = A(j, c) / sqrt(A(j, j)).  A
-// non-positive or NaN pivot records its global 1-based index in *flag and
-// stops.
-__global__ void __launch_bounds__(DIAG_THREADS) k_potrf_diag(double *B, int64_t ldb, int64_t k0, int kb, int nb,
-                                                             double *rdiag, int *flag) {
-  extern __shared__ double smem[];
-  double *v = smem + (size_t)(nb + 1) * nb;  // scaled pivot row A(j, c) / A(j, j)
-  double *u = v + nb;                         // unscaled pivot row A(j, r)
+// Cholesky of the pw x pw diagonal sub-block at (q0, q0), one warp: lane c
+// holds column c (rows 0..PW-1) in registers; the sub-block is padded to
+// PW x PW with the identity.  Step j: U(j, j) = sqrt(a_jj), the row
+// U(j, c) = a_jc / U(j, j), then a_rc -= U(j, r) U(j, c) for j < r <= c.
+__global__ void __launch_bounds__(32) k_chol_sub(double *B, int64_t ldb, int64_t q0, int pw, double *rd, int *flag) {
   if (*flag) return;
-  SmemBlock S{smem, nb + 1};
-  const int t = threadIdx.x;
-  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
-    int i = idx % kb, j = idx / kb;
-    S(i, j) = (i <= j) ? B[GS_IDX(k0 + i, k0 + j, ldb)] : 0.0;
-  }
-  __syncthreads();
+  const int c = threadIdx.x;
+  double a[PW];
+#pragma unroll
+  for (int r = 0; r < PW; r++) a[r] = (c < pw && r <= c) ? B[GS_IDX(q0 + r, q0 + c, ldb)] : (r == c ? 1.0 : 0.0);
+  double rmine = 1.0;
   int bad = 0;
-  for (int j = 0; j < kb; j++) {
-    const double d = S(j, j);  // every thread reads the same pivot: a uniform exit
+#pragma unroll
+  for (int j = 0; j < PW; j++) {
+    const double d = __shfl_sync(0xffffffffu, a[j], j);  // the same in every lane: uniform exit
     if (!(d > 0.0)) {
-      bad = (int)(k0 + j + 1);
+      bad = j + 1;
       break;
     }
-    const int w = kb - j - 1;
-    if (t < w) {
-      const double a = S(j, j + 1 + t);
-      u[t] = a;
-      v[t] = a * recip(d);
+    const double u = sqrt(d);
+    const double rj = 1.0 / u;
+    if (c == j) {
+      rmine = rj;
+      a[j] = u;
+    } else if (c > j) {
+      a[j] *= rj;
     }
-    __syncthreads();
-    // trailing update of the upper triangle, A(r, c) -= A(j, r) v(c) for
-    // j < r <= c: a warp per column, lanes down its rows, so no lane of the
-    // (narrow, per-lane) FP64 pipe idles on the lower triangle
-    for (int c = t >> 5; c < w; c += DIAG_THREADS / 32) {
-      const double vc = v[c];
-      for (int r = t & 31; r <= c; r += 32) S(j + 1 + r, j + 1 + c) = fma(-u[r], vc, S(j + 1 + r, j + 1 + c));
+#pragma unroll
+    for (int r = j + 1; r < PW; r++) {
+      const double ur = __shfl_sync(0xffffffffu, a[j], r);  // U(j, r)
+      if (c >= r) a[r] = fma(-ur, a[j], a[r]);
     }
-    __syncthreads();
   }
   if (bad) {
-    if (t == 0) atomicCAS(flag, 0, bad);
+    if (c == 0) atomicCAS(flag, 0, (int)(q0 + bad));
     return;
   }
-  // U(j, c) = A(j, c) / sqrt(A(j, j)) for c >= j
-  for (int j = t; j < kb; j += blockDim.x) {
-    const double sj = sqrt(S(j, j));
-    const double rs = 1.0 / sj;
-    rdiag[j] = rs;
-    v[j] = rs;
+  if (c < pw) {
+#pragma unroll
+    for (int r = 0; r < PW; r++)
+      if (r <= c) B[GS_IDX(q0 + r, q0 + c, ldb)] = a[r];
+    rd[c] = rmine;
+  }
+}
+
+// Rows q0..q0+pw-1 of the ncols columns from c0 on: x = U_pp^-T b by
+// forward substitution, x_j = b_j / U(j, j), then b_i -= U(j, i) x_j for
+// i > j; one warp per column (lane i holds row i), 8 columns per CTA.
+__global__ void __launch_bounds__(256) k_chol_panel(double *B, int64_t ldb, int64_t q0, int pw, int64_t c0, int ncols,
+                                                    const double *rd, const int *flag) {
+  if (*flag) return;
+  __shared__ double U[PW][PW + 1];  // U[j][i] = U(j, i)
+  __shared__ double ri[PW];
+  for (int idx = threadIdx.x; idx < PW * PW; idx += blockDim.x) {
+    const int j = idx % PW, i = idx / PW;
+    U[j][i] = (i < pw && j <= i) ? B[GS_IDX(q0 + j, q0 + i, ldb)] : 0.0;
+  }
+  if (threadIdx.x < PW) ri[threadIdx.x] = (threadIdx.x < pw) ? rd[threadIdx.x] : 0.0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cl = blockIdx.x * 8 + warp;
+  if (cl >= ncols) return;
+  const int64_t col = c0 + cl;
+  double b = (lane < pw) ? B[GS_IDX(q0 + lane, col, ldb)] : 0.0;
+  double x = 0.0;
+  for (int j = 0; j < pw; j++) {
+    const double xj = __shfl_sync(0xffffffffu, b, j) * ri[j];
+    if (lane == j) x = xj;
+    if (lane > j) b = fma(-U[j][lane], xj, b);
+  }
+  if (lane < pw) B[GS_IDX(q0 + lane, col, ldb)] = x;
+}
+
+// The rank-pw update of the upper triangle of the m x m block at (r0, r0):
+// A(r, c) -= sum_i U(q0 + i, r) U(q0 + i, c), r <= c, one 16 x 16 tile of
+// the upper triangle per CTA (tiles numbered row by row), one element per
+// thread.
+__global__ void __launch_bounds__(256) k_chol_update(double *B, int64_t ldb, int64_t q0, int pw, int64_t r0, int m,
+                                                     const int *flag) {
+  if (*flag) return;
+  const int nt = (m + 15) / 16;
+  int t = blockIdx.x, tr = 0;
+  while (tr < nt && t >= nt - tr) {
+    t -= nt - tr;
+    tr++;
+  }
+  const int tc = tr + t;
+  __shared__ double Ur[PW][17], Uc[PW][17];
+  for (int idx = threadIdx.x; idx < PW * 16; idx += blockDim.x) {
+    const int i = idx % PW, k = idx / PW;
+    const int rr = tr * 16 + k, cc = tc * 16 + k;
+    Ur[i][k] = (i < pw && rr < m) ? B[GS_IDX(q0 + i, r0 + rr, ldb)] : 0.0;
+    Uc[i][k] = (i < pw && cc < m) ? B[GS_IDX(q0 + i, r0 + cc, ldb)] : 0.0;
   }
   __syncthreads();
-  for (int idx = t; idx < kb * kb; idx += blockDim.x) {
-    const int i = idx % kb, j = idx / kb;
-    if (i < j) B[GS_IDX(k0 + i, k0 + j, ldb)] = S(i, j) * v[i];
-    else if (i == j) B[GS_IDX(k0 + i, k0 + j, ldb)] = S(i, i) * v[i];
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  const int r = tr * 16 + ty, c = tc * 16 + tx;
+  if (tr < nt && r < m && c < m && r <= c) {
+    double acc = B[GS_IDX(r0 + r, r0 + c, ldb)];
+    for (int i = 0; i < pw; i++) acc = fma(-Ur[i][ty], Uc[i][tx], acc);
+    B[GS_IDX(r0 + r, r0 + c, ldb)] = acc;
   }
 }
 
@@ -151,8 +187,12 @@ __global__ void __launch_bounds__(INV_WARPS * 32) k_trtri_cols(int64_t n, const 
     for (int m = 0; m < MR; m++)
       if (m == mk) bk = b[m];
     const double xk = __shfl_sync(0xffffffffu, bk, k & 31) * ri[k];
+    // rows 32 m + lane with m > k / 32 all lie below row k: nothing to do
+    // (k is the same in every lane, so the skip costs no divergence and the
+    // narrow FP64 pipe only sees the rows that change)
 #pragma unroll
     for (int m = 0; m < MR; m++) {
+      if (m > mk) break;
       const int i = lane + 32 * m;
       if (i < k) b[m] = fma(-S(i, k), xk, b[m]);
       else if (i == k) b[m] = xk;
@@ -165,7 +205,7 @@ __global__ void __launch_bounds__(INV_WARPS * 32) k_trtri_cols(int64_t n, const 
   }
 }
 
-// shared memory of both diagonal-block kernels: the block plus two rows
+// shared memory of k_trtri_cols: the block plus two rows
 size_t diag_smem_bytes(int nb) { return (size_t)(nb + 3) * nb * sizeof(double); }
 
 int set_smem(const void *fn, size_t bytes) {
@@ -218,7 +258,6 @@ int outer_inverse(cudaStream_t st, int64_t J0, int64_t jb, const double *U, int6
 // outer blocks would cost backward stability on badly scaled matrices).
 int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, FactorWork &w) {
   size_t sm = diag_smem_bytes(nb);
-  GS_TRY(set_smem((const void *)k_potrf_diag, sm));
   GS_TRY(set_smem((const void *)k_trtri_cols, sm));
   GS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
   w.outer_ready = false;
@@ -229,7 +268,7 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
   // inverted on the side stream, while the main stream applies the rest of
   // the same update with the persistent GEMM kept off kDiagSMs SMs.
   const bool la = w.side != nullptr && w.ev_upd != nullptr && w.ev_diag != nullptr;
-  constexpr int kDiagSMs = 9;  // k_potrf_diag (1 CTA) + k_trtri_cols (8 CTAs)
+  constexpr int kDiagSMs = 9;  // the k_chol_* launches (up to 36 small CTAs) and k_trtri_cols (8 CTAs)
   GemmContext *gc = current_gemm();
   const int ctas0 = gc ? gc->max_ctas : 0;
   auto reserve = [&](bool on) {
@@ -242,10 +281,21 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
     double *Uinv_k = w.Uinv + (size_t)(k0 / nb) * nb * nb;
     KernelProfiler *prof = current_profiler();
     const size_t e0 = prof ? prof->start(s) : SIZE_MAX;
-    k_potrf_diag<<<1, DIAG_THREADS, sm, s>>>(B, ldb, k0, kb, nb, w.rdiag, w.flag);
+    int launches = 1;
+    for (int p0 = 0; p0 < kb; p0 += PW) {
+      const int pw = std::min(PW, kb - p0), rest = kb - p0 - pw;
+      const int64_t q0 = k0 + p0;
+      k_chol_sub<<<1, 32, 0, s>>>(B, ldb, q0, pw, w.rdiag + p0, w.flag);
+      launches++;
+      if (rest <= 0) continue;
+      const int nt = (int)ceil_div(rest, 16);
+      k_chol_panel<<<(unsigned)ceil_div(rest, 8), 256, 0, s>>>(B, ldb, q0, pw, q0 + pw, rest, w.rdiag + p0, w.flag);
+      k_chol_update<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(B, ldb, q0, pw, q0 + pw, rest, w.flag);
+      launches += 2;
+    }
     k_trtri_cols<<<dim3((unsigned)ceil_div(nb, INV_WARPS), 1), INV_WARPS * 32, sm, s>>>(n, B, ldb, k0, nb, w.rdiag,
                                                                                         Uinv_k, w.flag);
-    count_launch(2);
+    count_launch(launches);
     GS_CHECK_LAUNCH();
     if (prof) prof->stop(s, e0, PROF_DIAG, 0.0, 0.0);
     return GSYEIG_SUCCESS;

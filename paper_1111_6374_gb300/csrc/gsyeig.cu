@@ -52,7 +52,7 @@ struct gsyeig_ctx {
   int device = 0;
   cudaStream_t user = nullptr;
   cudaStream_t st = nullptr;
-  cudaEvent_t ev[10] = {};  // 0-6 stage marks, 8 end mark, 9 user-stream ordering
+  cudaEvent_t ev[10] = {};  // 0-6 stage marks, 7 first host matrix landed, 8 end mark, 9 user-stream ordering
   gsyeig_opts opts{};
   // workspace
   DevBuf uinv, panel, flag, diag;
@@ -1427,12 +1427,16 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
                                   cudaMemcpyHostToDevice, s));
       return GSYEIG_SUCCESS;
     };
+    const auto tq0 = std::chrono::steady_clock::now();
     GS_TRY(h2d(d1, s1, l1, st));
     GS_CUDA(cudaEventRecord(h->cp_first, st));
+    GS_CUDA(cudaEventRecord(h->ev[7], st));
     GS_CUDA(cudaStreamWaitEvent(h->cp, h->cp_first, 0));
     GS_TRY(h2d(d2, s2, l2, h->cp));
     GS_CUDA(cudaEventRecord(h->cp_ev, h->cp));
     copy_pending.st = h->cp;
+    if (info)
+      info->host_ms_h2d_enqueue = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tq0).count();
   }
   // the second matrix has landed (no-op for device inputs)
   auto second_ready = [&]() -> int {
@@ -1656,6 +1660,7 @@ int gsyeig_solve(gsyeig_handle h, double *A, int64_t lda, double *B, int64_t ldb
     if (h->opts.mixed == 1) info->ms_refine = ke - info->ms_block_lanczos;  // the FP64 Lanczos stage
     info->ms_bt1 = elapsed(h->ev[4], h->ev[8]);
     info->ms_total = elapsed(h->ev[0], h->ev[8]);
+    if (hostA) info->ms_h2d_first = elapsed(h->ev[0], h->ev[7]);
     info->kernel_launches = g_launches.load() - l0;
     info->inverse = inv ? 1 : 0;
   }
