@@ -194,8 +194,9 @@ typedef struct {
    * flops of those launches */
   int64_t gemm_core_launches;
   double gemm_core_ms, gemm_core_flops;
-  /* opts.profile = 1: the kernels that factor and invert the nb x nb diagonal blocks of gs1 (pairs of
-   * launches) and their summed event time */
+  /* opts.profile = 1: the kernels that factor and invert the nb x nb diagonal blocks of gs1 (one
+   * group of launches per block: its Cholesky over sub-panels of 32 rows, then its inverse) and
+   * their summed event time */
   int64_t diag_launches;
   double diag_ms;
   double tnorm;           /* the recurrence's running estimate of ||T|| (bounds the operator's spectrum
@@ -255,7 +256,10 @@ const char *gsyeig_strerror(int status);
  * mu <= 0 is reported (GSYEIG_NOT_SPD with info.potrf_index = 0).
  * If dA and dB are HOST pointers the library copies them to its own device
  * workspace, leaves the host arrays unchanged, and dX must then be a host
- * pointer too (the result is copied back).  Returns GSYEIG_NOT_SPD,
+ * pointer too (the result is copied back).  Page-locked contiguous host
+ * matrices (ld = n, 16-byte aligned) are read by the library's own copy
+ * kernel through their device mapping, so each must hold n*n doubles;
+ * others go through cudaMemcpy(2D)Async.  Returns GSYEIG_NOT_SPD,
  * GSYEIG_NO_CONVERGENCE (best pairs still written), GSYEIG_TIMEOUT, ...
  */
 int gsyeig_solve(gsyeig_handle h, double *dA, int64_t lda, double *dB, int64_t ldb, int64_t n, int64_t s,
