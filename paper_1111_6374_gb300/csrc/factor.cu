@@ -27,60 +27,98 @@ struct SmemBlock {
 
 // The diagonal block B[k0:k0+kb, k0:k0+kb] (upper triangle) is factored in
 // place, B_kk = U_kk^T U_kk, by a right-looking Cholesky over sub-panels of
-// PW rows, three launches each: the PW x PW diagonal sub-block (one warp),
+// PW rows, three launches each: the PW x PW diagonal sub-block (one CTA),
 // the sub-panel's rows right of it (U_pp^-T times the block row, one warp
 // per column, many CTAs) and the rank-PW update of the rest of the block
 // (16 x 16 tiles of its upper triangle, many CTAs).  GB300's FP64 pipe is
 // narrow, so the flops of the block (kb^3/3) are spread over several SMs;
-// only the sub-blocks' O(PW^3) stay on one warp.  1 / U(i, i) is left in
+// only the sub-blocks' pivots stay serial.  1 / U(i, i) is left in
 // rdiag[0..kb).  A non-positive or NaN pivot records its global 1-based
 // index in *flag and stops; every later launch of the block (and every GEMM
 // given the flag) then returns at once.  Only the upper triangle of the
 // block is written.
 constexpr int PW = 32;
 
-// Cholesky of the pw x pw diagonal sub-block at (q0, q0), one warp: lane c
-// holds column c (rows 0..PW-1) in registers; the sub-block is padded to
-// PW x PW with the identity.  Step j: U(j, j) = sqrt(a_jj), the row
-// U(j, c) = a_jc / U(j, j), then a_rc -= U(j, r) U(j, c) for j < r <= c.
-__global__ void __launch_bounds__(32) k_chol_sub(double *B, int64_t ldb, int64_t q0, int pw, double *rd, int *flag) {
+// 1/d to within about an ulp for any positive finite d: d = f 2^k with f in
+// [1/2, 1) (frexp, exact), an fp32 seed of 1/f refined by two Newton steps
+// in FP64, scaled back by 2^-k (ldexp, exact unless the result leaves the
+// FP64 range).  GB300's FP64 divide is a long sequence on a narrow pipe; this
+// takes four FP64 FMAs.
+__device__ __forceinline__ double recip(double d) {
+  int k;
+  const double f = frexp(d, &k);
+  double r = (double)(1.0f / (float)f);
+  double e = fma(-f, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-f, r, 1.0);
+  r = fma(r, e, r);
+  return ldexp(r, -k);
+}
+
+// Cholesky of the pw x pw diagonal sub-block at (q0, q0), padded to PW x PW
+// with the identity, on one CTA of four warps (one per SMSP) in shared
+// memory.  Right-looking on the unscaled rows: step j updates
+// A(r, c) -= A(j, r) A(j, c) / A(j, j) for j < r <= c, with the active
+// trailing triangle packed over all 128 threads (the elements are listed by
+// row, last row first, so that step j's are the first (31-j)(32-j)/2), and
+// only the pivot's reciprocal is serial.  At the end U(r, c) = A(r, c) /
+// sqrt(A(r, r)).
+constexpr int SUB_T = 128;
+constexpr int SUB_ELEMS = PW * (PW - 1) / 2;  // (r, c), 1 <= r <= c < PW
+__global__ void __launch_bounds__(SUB_T) k_chol_sub(double *B, int64_t ldb, int64_t q0, int pw, double *rd, int *flag) {
   if (*flag) return;
-  const int c = threadIdx.x;
-  double a[PW];
-#pragma unroll
-  for (int r = 0; r < PW; r++) a[r] = (c < pw && r <= c) ? B[GS_IDX(q0 + r, q0 + c, ldb)] : (r == c ? 1.0 : 0.0);
-  double rmine = 1.0;
+  __shared__ double S[PW][PW + 1];  // S[c][r] = A(r, c)
+  __shared__ double u[PW], v[PW];
+  __shared__ unsigned char er[SUB_ELEMS], ec[SUB_ELEMS];
+  const int t = threadIdx.x;
+  for (int idx = t; idx < PW * PW; idx += SUB_T) {
+    const int r = idx % PW, c = idx / PW;
+    S[c][r] = (c < pw && r <= c) ? B[GS_IDX(q0 + r, q0 + c, ldb)] : (r == c ? 1.0 : 0.0);
+  }
+  for (int e = t; e < SUB_ELEMS; e += SUB_T) {
+    int r = PW - 1, base = 0;  // row r holds PW - r elements, rows PW-1, PW-2, ... first
+    while (e >= base + (PW - r)) {
+      base += PW - r;
+      r--;
+    }
+    er[e] = (unsigned char)r;
+    ec[e] = (unsigned char)(r + (e - base));
+  }
+  __syncthreads();
   int bad = 0;
-#pragma unroll
   for (int j = 0; j < PW; j++) {
-    const double d = __shfl_sync(0xffffffffu, a[j], j);  // the same in every lane: uniform exit
+    const double d = S[j][j];  // the same in every thread: a uniform exit
     if (!(d > 0.0)) {
       bad = j + 1;
       break;
     }
-    const double u = sqrt(d);
-    const double rj = 1.0 / u;
-    if (c == j) {
-      rmine = rj;
-      a[j] = u;
-    } else if (c > j) {
-      a[j] *= rj;
+    if (t < PW) {
+      const double a = (t > j) ? S[t][j] : 0.0;  // A(j, t)
+      u[t] = a;
+      v[t] = a * recip(d);
     }
-#pragma unroll
-    for (int r = j + 1; r < PW; r++) {
-      const double ur = __shfl_sync(0xffffffffu, a[j], r);  // U(j, r)
-      if (c >= r) a[r] = fma(-ur, a[j], a[r]);
+    __syncthreads();
+    const int nact = (PW - 1 - j) * (PW - j) / 2;
+    for (int e = t; e < nact; e += SUB_T) {
+      const int r = er[e], c = ec[e];
+      S[c][r] = fma(-u[r], v[c], S[c][r]);
     }
+    __syncthreads();
   }
   if (bad) {
-    if (c == 0) atomicCAS(flag, 0, (int)(q0 + bad));
+    if (t == 0) atomicCAS(flag, 0, (int)(q0 + bad));
     return;
   }
-  if (c < pw) {
-#pragma unroll
-    for (int r = 0; r < PW; r++)
-      if (r <= c) B[GS_IDX(q0 + r, q0 + c, ldb)] = a[r];
-    rd[c] = rmine;
+  if (t < PW) {
+    const double sq = sqrt(S[t][t]);
+    u[t] = sq;
+    v[t] = 1.0 / sq;
+    if (t < pw) rd[t] = v[t];
+  }
+  __syncthreads();
+  for (int idx = t; idx < PW * PW; idx += SUB_T) {
+    const int r = idx % PW, c = idx / PW;
+    if (c < pw && r <= c) B[GS_IDX(q0 + r, q0 + c, ldb)] = (r == c) ? u[r] : S[c][r] * v[r];
   }
 }
 
@@ -285,7 +323,7 @@ int potrf_blocked(cudaStream_t st, int64_t n, double *B, int64_t ldb, int nb, Fa
     for (int p0 = 0; p0 < kb; p0 += PW) {
       const int pw = std::min(PW, kb - p0), rest = kb - p0 - pw;
       const int64_t q0 = k0 + p0;
-      k_chol_sub<<<1, 32, 0, s>>>(B, ldb, q0, pw, w.rdiag + p0, w.flag);
+      k_chol_sub<<<1, SUB_T, 0, s>>>(B, ldb, q0, pw, w.rdiag + p0, w.flag);
       launches++;
       if (rest <= 0) continue;
       const int nt = (int)ceil_div(rest, 16);
